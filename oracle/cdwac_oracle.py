@@ -1,0 +1,434 @@
+"""Plain FP64 CPU oracle for contour-deformation G0W0 of core levels: plain CD and CD-WAC.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  It shares no code with the CUDA library and never calls it.
+
+Every function follows one passage of Panades-Barrueta & Golze, "Accelerating core-level GW calculations by
+combining the contour deformation approach with the analytic continuation of W" (arXiv 2305.15955), written
+in the paper's order and notation.  Library primitives (matrix products, Cholesky and LU factorisations,
+Gauss-Legendre nodes, a symmetric eigensolver) serve as single steps; nothing is blocked, fused or reordered.
+
+Conventions (readings of points the paper leaves open):
+  * closed shell, spin factor 2 in the polarizability (Eq. piriv carries none; Sec. 2.1 drops spin);
+  * the imaginary-axis grid is Gauss-Legendre on (-1, 1) mapped by xi = omega0 (1 + x) / (1 - x);
+  * the Fermi level is the middle of the HOMO-LUMO gap; occupations are fixed by orbital index;
+  * theta(0) = 1/2 in the residue factors f_m (Eq. ffact);
+  * complex arguments z = x + i*eta carry the infinitesimal of Eq. piriv, so
+    Pi(z) = 2 sum_ia O^ia [1/(z - D_ia) - 1/(z + D_ia)] O^ia, an even function of z;
+  * greedy Thiele: the first node maximises |W|, every later node maximises the L1 error
+    |Re(T - W)| + |Im(T - W)| of the current convergent over the remaining nodes; ties go to the lowest
+    candidate index; a node whose reciprocal difference is not finite ends the fit (breakdown).
+
+Parity pins (tests/test_oracle_pins.py): the sum-over-poles self-energy of Eq. sigma_pole from a full RPA
+diagonalisation, the closed-form one-pole system, Gauss-Legendre exactness and known integrals,
+Thiele interpolation and one-pole exactness, invariants of Pi, Lambda and W.  The CD-WAC continuation error
+itself has no exact pin: it is a measured quantity of the method.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import scipy.linalg
+
+# ---------------------------------------------------------------------------------------------------------
+# Frequency grids and occupations
+# ---------------------------------------------------------------------------------------------------------
+
+
+def imaginary_grid(n_imag: int, omega0: float = 1.0):
+    """Modified Gauss-Legendre grid on [0, inf) for the I_n quadrature (Sec. 4, 'modified Gauss-Legendre grid').
+
+    x_k, w_k are the n-point Gauss-Legendre nodes and weights on (-1, 1); xi_k = omega0 (1+x_k)/(1-x_k) and the
+    weight carries the Jacobian d xi / d x = 2 omega0 / (1 - x)^2.  Returns (xi, wxi), xi ascending.
+    """
+    x, w = np.polynomial.legendre.leggauss(n_imag)
+    xi = omega0 * (1.0 + x) / (1.0 - x)
+    wxi = w * 2.0 * omega0 / (1.0 - x) ** 2
+    return xi, wxi
+
+
+def fermi_level(eps, n_occ):
+    """epsilon_F read as the middle of the HOMO-LUMO gap (the paper gives no number)."""
+    return 0.5 * (eps[n_occ - 1] + eps[n_occ])
+
+
+def transition_energies(eps, n_occ):
+    """D_ia = eps_a - eps_i, flattened as ia = i * n_virt + a (the column order of O^{ia}_P)."""
+    return (eps[None, n_occ:] - eps[:n_occ, None]).reshape(-1)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Screened Coulomb interaction in RI-V (Eqs. piriv, bigLambda, wriv; Sec. 2.3)
+# ---------------------------------------------------------------------------------------------------------
+
+
+def polarizability(B, D, z):
+    """Pi_PQ(z), Eq. piriv with spin factor 2: 2 sum_ia O^ia_P [1/(z - D_ia) - 1/(z + D_ia)] O^ia_Q.
+
+    B is O^{ia}_P as an [N_aux, N_occ*N_virt] array, D the matching D_ia.  For purely imaginary z the
+    bracket is real (-2 D / (xi^2 + D^2)) and a real matrix is returned.
+    """
+    z = complex(z)
+    if z.real == 0.0:
+        # z = i xi: 1/(i xi - D) - 1/(i xi + D) = -2 D / (xi^2 + D^2), real
+        w = 2.0 * (-2.0 * D / (z.imag ** 2 + D ** 2))
+    else:
+        w = 2.0 * (1.0 / (z - D) - 1.0 / (z + D))
+    return (B * w[None, :]) @ B.T
+
+
+def screened_lambda(Pi):
+    """Lambda = (I - Pi)^{-1} - I, Eq. bigLambda.
+
+    On the imaginary axis I - Pi is real symmetric positive definite (Pi is negative semidefinite) and is
+    inverted through its Cholesky factor; elsewhere it is complex symmetric and an LU factorisation with
+    partial pivoting is used.
+    """
+    n = Pi.shape[0]
+    A = np.eye(n, dtype=Pi.dtype) - Pi
+    if np.isrealobj(A):
+        c = scipy.linalg.cho_factor(A, lower=True)
+        Ainv = scipy.linalg.cho_solve(c, np.eye(n))
+    else:
+        lu = scipy.linalg.lu_factor(A)
+        Ainv = scipy.linalg.lu_solve(lu, np.eye(n, dtype=A.dtype))
+    return Ainv - np.eye(n)
+
+
+def w_elements(On_s, Lam, m_idx=None):
+    """W^c_nm = sum_PQ O^{nm}_P Lambda_PQ O^{mn}_Q, Eq. wriv, for one state n and orbitals m.
+
+    On_s is O^{n m}_P as [N_aux, N_basis] (symmetric in n, m).  Returns W for every m (or for m_idx).
+    """
+    O = On_s if m_idx is None else On_s[:, m_idx]
+    return np.einsum("pm,pq,qm->m", O, Lam, O)
+
+
+def w_imag_table(B, D, On, xi):
+    """W_nm(i xi_k) for all states n, all k, all m: the wmatrix(F_Im) step (Sec. 3.4).  [n_states, n_xi, N_b]."""
+    n_states, _, nb = On.shape
+    W = np.empty((n_states, len(xi), nb))
+    for k, x in enumerate(xi):
+        Lam = screened_lambda(polarizability(B, D, 1j * x))
+        for s in range(n_states):
+            W[s, k] = w_elements(On[s], Lam)
+    return W
+
+
+def w_complex_table(B, D, On, z_list, m_idx):
+    """W_nm(z_j) for complex points z_j and orbitals m_idx: the wmatrix(F_real) step.  [n_states, n_z, len(m)]."""
+    n_states = On.shape[0]
+    W = np.empty((n_states, len(z_list), len(m_idx)), dtype=complex)
+    for j, z in enumerate(z_list):
+        Lam = screened_lambda(polarizability(B, D, z))
+        for s in range(n_states):
+            W[s, j] = w_elements(On[s], Lam, m_idx)
+    return W
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Self-energy by contour deformation (Eqs. cdmain, In_term, Rn_term, ffact, cdselfe; Sec. 2.3)
+# ---------------------------------------------------------------------------------------------------------
+
+
+def occupation_sign(eps, n_occ):
+    """sgn(eps_F - eps_m): +1 for occupied m, -1 for virtual m."""
+    s = -np.ones(len(eps))
+    s[:n_occ] = 1.0
+    return s
+
+
+def sigma_I(W_imag_s, eps, n_occ, xi, wxi, omega, eta):
+    """I_n(omega), Eq. In_term, for one state from its W_nm(i xi_k) table [n_xi, N_b].
+
+    W(i w') is even in w', so the integral over the whole imaginary axis is folded onto [0, inf):
+    1/(2 pi) int dw' W(iw') / (a + iw') = 1/(2 pi) int_0^inf dw' W(iw') [1/(a + iw') + 1/(a - iw')],
+    with a_m = omega - eps_m - i eta sgn(eps_F - eps_m).
+    """
+    a = omega - eps - 1j * eta * occupation_sign(eps, n_occ)          # [N_b]
+    kern = 1.0 / (a[None, :] + 1j * xi[:, None]) + 1.0 / (a[None, :] - 1j * xi[:, None])   # [n_xi, N_b]
+    return np.sum(wxi[:, None] * W_imag_s * kern) / (2.0 * np.pi)
+
+
+def residue_factors(eps, n_occ, omega):
+    """f_m of Eq. ffact: -theta(eF - e_m) theta(e_m - w) + theta(e_m - eF) theta(w - e_m), theta(0) = 1/2."""
+    th = lambda x: np.where(x > 0, 1.0, np.where(x < 0, 0.0, 0.5))
+    occ = np.zeros(len(eps))
+    occ[:n_occ] = 1.0
+    return -occ * th(eps - omega) + (1.0 - occ) * th(omega - eps)
+
+
+def sigma_R_cd(B, D, On_s, eps, n_occ, omega, eta):
+    """R_n(omega), Eq. Rn_term, plain CD: W_nm built directly at every residue |eps_m - omega| + i eta."""
+    f = residue_factors(eps, n_occ, omega)
+    R = 0.0 + 0.0j
+    for m in np.nonzero(f)[0]:
+        z = abs(eps[m] - omega) + 1j * eta
+        Lam = screened_lambda(polarizability(B, D, z))
+        R += f[m] * w_elements(On_s, Lam, [m])[0]
+    return R
+
+
+def sigma_c_cd(B, D, On_s, W_imag_s, eps, n_occ, xi, wxi, omega, eta):
+    """Sigma^c_n(omega) = R_n - I_n (Eq. cdselfe without the static exchange), plain CD."""
+    return sigma_R_cd(B, D, On_s, eps, n_occ, omega, eta) - sigma_I(W_imag_s, eps, n_occ, xi, wxi, omega, eta)
+
+
+def sigma_x(On_s, n_occ):
+    """Static exchange in RI-V, Eq. exs: Sigma^x_n = -sum_i^occ (ni|in) = -sum_i sum_P (O^{ni}_P)^2."""
+    return -np.sum(On_s[:, :n_occ] ** 2)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Analytic continuation of W: greedy Thiele reciprocal differences (Eqs. pade, pre_rec, rec_eq; Sec. 3.2)
+# ---------------------------------------------------------------------------------------------------------
+
+
+def thiele_eval(a, z2_nodes, z):
+    """T^M(z), Eq. pade: a_1 / (1 + a_2 (z^2 - zt_1^2) / (1 + ... a_M (z^2 - zt_{M-1}^2))).
+
+    Evaluated from the innermost level outwards.  a has M entries, z2_nodes the M node values zt_p^2.
+    """
+    z2 = np.asarray(z, dtype=complex) ** 2
+    t = np.ones_like(z2)
+    for p in range(len(a) - 1, 0, -1):            # levels M .. 2 (0-based p = M-1 .. 1)
+        t = 1.0 + a[p] * (z2 - z2_nodes[p - 1]) / t
+    return a[0] / t
+
+
+@dataclasses.dataclass
+class ThieleFit:
+    nodes: list            # candidate indices in the order they entered the fraction
+    a: np.ndarray          # complex coefficients a_1..a_M
+    z2: np.ndarray         # zt_p^2 of the chosen nodes
+    breakdown: bool        # True if the fit stopped early on a non-finite reciprocal difference
+
+
+def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
+    """Greedy Thiele interpolation of W over candidate nodes z (Sec. 3.2, the greedy procedure).
+
+    g_1(z_i) = W(z_i); g_p(z_i) = (g_{p-1}(zt_{p-1}) - g_{p-1}(z_i)) / ((z_i^2 - zt_{p-1}^2) g_{p-1}(z_i)) (Eq. rec_eq),
+    a_p = g_p(zt_p) (Eq. pre_rec).  The first node is argmax |W|; node p >= 2 is the remaining candidate with the
+    largest (criterion 'max') or smallest ('min') L1 error of the convergent T^{p-1}.  Stops after M nodes.
+    """
+    z = np.asarray(z, dtype=complex)
+    W = np.asarray(W, dtype=complex)
+    z2 = z ** 2
+    n = len(z)
+    M = min(M, n)
+    g = W.copy()                                   # g_1 at every candidate
+    remaining = np.ones(n, dtype=bool)
+    if first == "absmax":
+        k = int(np.argmax(np.abs(W)))
+    elif first == "max":
+        k = int(np.argmax(W.real))
+    else:
+        k = 0
+    nodes = [k]
+    a = [g[k]]
+    remaining[k] = False
+    breakdown = False
+    for p in range(2, M + 1):
+        rem = np.nonzero(remaining)[0]
+        if len(rem) == 0:
+            break
+        zt2_prev = z2[nodes[-1]]
+        a_prev = a[-1]
+        with np.errstate(all="ignore"):
+            g[rem] = (a_prev - g[rem]) / ((z2[rem] - zt2_prev) * g[rem])
+            T = thiele_eval(np.array(a), z2[np.array(nodes)], z[rem])
+            err = np.abs((T - W[rem]).real) + np.abs((T - W[rem]).imag)
+        err = np.where(np.isfinite(err), err, np.inf)
+        pick = int(np.argmax(err)) if criterion == "max" else int(np.argmin(err))
+        k = int(rem[pick])
+        if not np.isfinite(g[k]):
+            breakdown = True
+            break
+        nodes.append(k)
+        a.append(g[k])
+        remaining[k] = False
+    return ThieleFit(nodes=nodes, a=np.array(a, dtype=complex), z2=z2[np.array(nodes)], breakdown=breakdown)
+
+
+def near_real_points(eps, n_occ, eps_n, n_real, eta_ref=1e-3, margin=0.5):
+    """Generic near-real reference set omega_G (Sec. 3.3): n_real equidistant points x_j + i eta_ref with
+    x_j spanning [0, |eps_F - eps_n| + margin], i.e. every residue |eps_m - omega| up to the Fermi level."""
+    if n_real == 0:
+        return np.zeros(0, dtype=complex)
+    top = abs(fermi_level(eps, n_occ) - eps_n) + margin
+    x = np.linspace(0.0, top, n_real)
+    return x + 1j * eta_ref
+
+
+@dataclasses.dataclass
+class WacModel:
+    """CD-WAC continuation of one state: one Thiele fit per occupied m."""
+    fits: list             # ThieleFit per occupied m (index = m)
+
+
+def fit_wac(W_imag_s, W_real_s, xi, z_real, n_occ, M, first="absmax", criterion="max"):
+    """The AC step (Sec. 3.4): for each occupied m, fit W_nm over F_wac = F_Im U F_real."""
+    fits = []
+    zc = np.concatenate([1j * np.asarray(xi), np.asarray(z_real, dtype=complex)])
+    for m in range(n_occ):
+        Wc = np.concatenate([W_imag_s[:, m].astype(complex), W_real_s[:, m] if len(z_real) else np.zeros(0)])
+        fits.append(thiele_greedy_fit(zc, Wc, M, first, criterion))
+    return WacModel(fits=fits)
+
+
+def sigma_R_wac(model, eps, n_occ, omega, eta):
+    """R_n(omega), Eq. Rn_term, with W_nm(|eps_m - omega| + i eta) replaced by T^M_nm (occupied m only)."""
+    f = residue_factors(eps, n_occ, omega)
+    R = 0.0 + 0.0j
+    for m in np.nonzero(f)[0]:
+        if m >= n_occ:
+            raise ValueError("CD-WAC continuation covers occupied residues only (omega below the LUMO)")
+        fit = model.fits[m]
+        R += f[m] * thiele_eval(fit.a, fit.z2, abs(eps[m] - omega) + 1j * eta)
+    return complex(R)
+
+
+def sigma_c_wac(model, W_imag_s, eps, n_occ, xi, wxi, omega, eta):
+    """Sigma^c_n(omega) = R_n - I_n with the continued residue term (CD-WAC)."""
+    return sigma_R_wac(model, eps, n_occ, omega, eta) - sigma_I(W_imag_s, eps, n_occ, xi, wxi, omega, eta)
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Quasiparticle equation (Eq. qp_eq) and the sum-over-poles self-energy (Eq. sigma_pole)
+# ---------------------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class QPResult:
+    e_qp: float
+    Z: float
+    iterations: int
+    status: int            # 0 converged by fixed point, 1 by bracketed bisection, 2 not converged
+
+
+def qp_solve(sigma_fn, eps_n, shift, omega_grid, tol=1e-7, max_iter=100, h=1e-5, bisect_tol=1e-9):
+    """Solve e = eps_n + shift + Re Sigma^c_n(e) (Eq. qp_eq with shift = Sigma^x_n - v^xc_n).
+
+    Fixed-point iteration from eps_n until |e_new - e| < tol.  If it does not converge, every sign change of
+    f(w) = w - eps_n - shift - Re Sigma(w) between neighbouring points of omega_grid is bisected to bisect_tol;
+    roots with |f| < 1e-6 are kept and the one with the largest Z in (0, 1] is returned.
+    Z = 1 / (1 - d Re Sigma / d w) by a central difference of step h.
+    """
+    def zfac(e):
+        d = (sigma_fn(e + h).real - sigma_fn(e - h).real) / (2.0 * h)
+        return 1.0 / (1.0 - d)
+
+    e = eps_n
+    for it in range(1, max_iter + 1):
+        e_new = eps_n + shift + sigma_fn(e).real
+        if abs(e_new - e) < tol:
+            return QPResult(e_new, zfac(e_new), it, 0)
+        e = e_new
+    f = lambda w: w - eps_n - shift - sigma_fn(w).real
+    fv = np.array([f(w) for w in omega_grid])
+    best = None
+    for j in range(len(omega_grid) - 1):
+        if fv[j] == 0.0 or fv[j] * fv[j + 1] < 0:
+            lo, hi, flo = omega_grid[j], omega_grid[j + 1], fv[j]
+            while hi - lo > bisect_tol:
+                mid = 0.5 * (lo + hi)
+                fm = f(mid)
+                if fm * flo <= 0:
+                    hi = mid
+                else:
+                    lo, flo = mid, fm
+            r = 0.5 * (lo + hi)
+            if abs(f(r)) < 1e-6:
+                Zr = zfac(r)
+                if 0.0 < Zr <= 1.0 and (best is None or Zr > best[1]):
+                    best = (r, Zr)
+    if best is not None:
+        return QPResult(best[0], best[1], max_iter, 1)
+    return QPResult(e, zfac(e), max_iter, 2)
+
+
+def rpa_poles(B, D):
+    """Neutral excitations of direct RPA in RI form: Omega_s^2 and eigenvectors of
+    C = D^2 + 4 D^{1/2} B^T B D^{1/2} (closed shell), the Omega_s of Eq. sigma_pole."""
+    sq = np.sqrt(D)
+    C = np.diag(D ** 2) + 4.0 * (sq[:, None] * (B.T @ B) * sq[None, :])
+    Om2, Z = np.linalg.eigh(C)
+    return np.sqrt(Om2), Z
+
+
+def pole_amplitudes(B, D, On_s, Omega, Z):
+    """w^s_nm with (w^s_nm)^2 = <nm|P_s|mn> of Eq. sigma_pole: w^s_nm = sqrt(2) sum_ia (O^{nm} . O^{ia}) D^{1/2} Z_ia,s / sqrt(Omega_s).
+    Returns [N_basis, n_poles]."""
+    v = (On_s.T @ B) * np.sqrt(D)[None, :]          # [N_b, N_ov]
+    return np.sqrt(2.0) * (v @ Z) / np.sqrt(Omega)[None, :]
+
+
+def sigma_c_pole_sum(B, D, On_s, eps, n_occ, omega, eta):
+    """Sigma^c_n(omega) by the sum over poles, Eq. sigma_pole (the fully analytic O(N^6) route)."""
+    Omega, Z = rpa_poles(B, D)
+    wamp = pole_amplitudes(B, D, On_s, Omega, Z)
+    sgn = occupation_sign(eps, n_occ)
+    den = omega - eps[:, None] + (Omega[None, :] - 1j * eta) * sgn[:, None]
+    return np.sum(wamp ** 2 / den)
+
+
+def w_imag_pole_sum(B, D, On_s, xi):
+    """W^c_nm(i xi) = -sum_s (w^s_nm)^2 2 Omega_s / (xi^2 + Omega_s^2), the pole form of W behind Eq. sigma_pole."""
+    Omega, Z = rpa_poles(B, D)
+    wamp = pole_amplitudes(B, D, On_s, Omega, Z)
+    xi = np.atleast_1d(xi)
+    return -np.einsum("ms,ks->km", wamp ** 2, 2.0 * Omega[None, :] / (xi[:, None] ** 2 + Omega[None, :] ** 2))
+
+
+# ---------------------------------------------------------------------------------------------------------
+# The whole procedure (Sec. 3.4): CD and CD-WAC G0W0 for a list of states
+# ---------------------------------------------------------------------------------------------------------
+
+
+@dataclasses.dataclass
+class Params:
+    n_imag: int = 100
+    omega0: float = 1.0
+    n_real: int = 40
+    eta_ref: float = 1e-3
+    eta: float = 1e-3
+    pade_M: int = 64
+    greedy_first: str = "absmax"
+    greedy_criterion: str = "max"
+    real_margin: float = 0.5
+
+
+def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None, with_sigma=True):
+    """CD-WAC G0W0 (Sec. 3.4): W on the imaginary grid, W at the near-real points, greedy Thiele fit per
+    occupied m, Sigma^c on omega_grid and the QP solution per state."""
+    xi, wxi = imaginary_grid(params.n_imag, params.omega0)
+    Wim = w_imag_table(B, D, On, xi)
+    out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "states": []}
+    for s, n in enumerate(states):
+        zr = near_real_points(eps, n_occ, eps[n], params.n_real, params.eta_ref, params.real_margin)
+        Wre = w_complex_table(B, D, On[s:s + 1], zr, np.arange(n_occ))[0] if len(zr) else np.zeros((0, n_occ), complex)
+        model = fit_wac(Wim[s], Wre, xi, zr, n_occ, params.pade_M, params.greedy_first, params.greedy_criterion)
+        sig = lambda w, s=s, model=model: sigma_c_wac(model, Wim[s], eps, n_occ, xi, wxi, w, params.eta)
+        sh = 0.0 if shifts is None else shifts[s]
+        res = {"n": n, "z_real": zr, "W_real": Wre, "model": model,
+               "qp": qp_solve(sig, eps[n], sh, omega_grid)}
+        if with_sigma:
+            res["sigma"] = np.array([sig(w) for w in omega_grid])
+        out["states"].append(res)
+    return out
+
+
+def run_cd(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None, with_sigma=True):
+    """Plain CD G0W0 (Sec. 3.4): the residue term builds W at every residue of every frequency."""
+    xi, wxi = imaginary_grid(params.n_imag, params.omega0)
+    Wim = w_imag_table(B, D, On, xi)
+    out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "states": []}
+    for s, n in enumerate(states):
+        sig = lambda w, s=s: sigma_c_cd(B, D, On[s], Wim[s], eps, n_occ, xi, wxi, w, params.eta)
+        sh = 0.0 if shifts is None else shifts[s]
+        res = {"n": n, "qp": qp_solve(sig, eps[n], sh, omega_grid)}
+        if with_sigma:
+            res["sigma"] = np.array([sig(w) for w in omega_grid])
+        out["states"].append(res)
+    return out

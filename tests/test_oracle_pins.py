@@ -1,0 +1,224 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: the fully analytic sum-over-poles
+self-energy (Eq. sigma_pole) from an RPA diagonalisation, closed forms, exactness of Gauss-Legendre and of
+rational interpolation, and invariants of Pi, Lambda and W (Sec. 2.3).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cdwac_oracle as o
+from paper_2305_15955_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def small():
+    spec = inputs.small_system()
+    eps = inputs.eigenvalues(spec)
+    B = inputs.build_B(spec)
+    On = inputs.build_On(spec)
+    D = o.transition_energies(eps, spec.n_occ)
+    xi, wxi = o.imaginary_grid(100)
+    Wim = o.w_imag_table(B, D, On, xi)
+    return dict(spec=spec, eps=eps, B=B, On=On, D=D, xi=xi, wxi=wxi, Wim=Wim)
+
+
+# --- grid -------------------------------------------------------------------------------------------------
+
+def test_imaginary_grid_exact_rational_integrals():
+    # xi = (1+x)/(1-x) turns 1/(1+xi)^2 and 1/(1+xi)^4 into polynomials of x: Gauss-Legendre is exact
+    for n in (4, 17, 100):
+        xi, w = o.imaginary_grid(n)
+        assert np.all(np.diff(xi) > 0) and xi[0] > 0
+        assert abs(np.sum(w / (1 + xi) ** 2) - 1.0) < 1e-13
+        assert abs(np.sum(w / (1 + xi) ** 4) - 1.0 / 3.0) < 1e-13
+    xi, w = o.imaginary_grid(100, omega0=2.5)
+    assert abs(np.sum(w / (2.5 + xi) ** 2) - 1.0 / 2.5) < 1e-13
+
+
+def test_imaginary_grid_lorentzian():
+    xi, w = o.imaginary_grid(100)
+    for a in (0.3, 1.0, 10.6):
+        assert abs(np.sum(w * a / (a * a + xi * xi)) - math.pi / 2) < 1e-6
+
+
+def test_transition_energy_order():
+    eps = np.array([-3.0, -1.0, 0.5, 2.0, 7.0])
+    D = o.transition_energies(eps, 2)
+    expect = [eps[a] - eps[i] for i in range(2) for a in range(2, 5)]
+    assert np.array_equal(D, np.array(expect))
+
+
+def test_residue_factors_cases():
+    eps = np.array([-10.0, -1.0, 0.5, 2.0])
+    f = o.residue_factors(eps, 2, -5.0)      # occupied m above omega contributes -1
+    assert list(f) == [0.0, -1.0, 0.0, 0.0]
+    f = o.residue_factors(eps, 2, 1.0)       # virtual m below omega contributes +1
+    assert list(f) == [0.0, 0.0, 1.0, 0.0]
+    f = o.residue_factors(eps, 2, -1.0)      # theta(0) = 1/2
+    assert list(f) == [0.0, -0.5, 0.0, 0.0]
+
+
+# --- screened interaction -------------------------------------------------------------------------------
+
+def test_pi_invariants(small):
+    B, D = small["B"], small["D"]
+    for x in (0.01, 1.0, 300.0):
+        Pi = o.polarizability(B, D, 1j * x)
+        assert np.isrealobj(Pi)
+        assert np.abs(Pi - Pi.T).max() < 1e-14
+        ev = np.linalg.eigvalsh(Pi)
+        assert ev.max() < 1e-12                          # negative semidefinite
+        Lam = o.screened_lambda(Pi)
+        assert np.linalg.eigvalsh(0.5 * (Lam + Lam.T)).max() < 1e-12
+        assert np.linalg.eigvalsh(0.5 * (Lam + Lam.T)).min() > -1.0
+    # even in the frequency: Pi(z) = Pi(-z) for complex z
+    z = 0.7 + 0.05j
+    assert np.abs(o.polarizability(B, D, z) - o.polarizability(B, D, -z)).max() < 1e-13
+
+
+def test_w_imag_invariants(small):
+    W = small["Wim"][0]                                   # [n_xi, N_b]
+    assert np.all(W <= 1e-15)
+    assert np.all(np.diff(W, axis=0) >= -1e-15)            # increasing towards 0 with xi
+    assert np.abs(W[-1]).max() < 1e-4 * np.abs(W[0]).max()
+
+
+def test_w_imag_matches_rpa_pole_form(small):
+    s = small
+    Wp = o.w_imag_pole_sum(s["B"], s["D"], s["On"][0], s["xi"])
+    assert np.abs(s["Wim"][0] - Wp).max() < 1e-13
+
+
+def test_one_pole_closed_form():
+    # N_aux = 1, one transition: W(z) = 4 o^2 b^2 D / (z^2 - D^2 - 4 b^2 D)
+    b, d, ov = 0.7, 0.9, 0.4
+    B = np.array([[b]])
+    D = np.array([d])
+    for z in (0.3j, 2.0j, 0.5 + 0.01j, 1.7 + 0.001j):
+        Lam = o.screened_lambda(o.polarizability(B, D, z))
+        W = o.w_elements(np.array([[ov]]), Lam)[0]
+        expect = 4 * ov ** 2 * b ** 2 * d / (z ** 2 - d ** 2 - 4 * b ** 2 * d)
+        assert abs(W - expect) < 1e-14
+
+
+# --- self-energy: plain CD is exact against the sum over poles ---------------------------------------------
+
+@pytest.mark.parametrize("omega", [-11.0, -10.7, -10.45, -10.2, -10.0, -0.2, 0.011, 0.5, 2.6])
+def test_cd_matches_sum_over_poles(small, omega):
+    s = small
+    eta = 1e-8
+    cd = o.sigma_c_cd(s["B"], s["D"], s["On"][0], s["Wim"][0], s["eps"], s["spec"].n_occ, s["xi"], s["wxi"],
+                      omega, eta)
+    ps = o.sigma_c_pole_sum(s["B"], s["D"], s["On"][0], s["eps"], s["spec"].n_occ, omega, eta)
+    assert abs(cd.real - ps.real) < 1e-10 * max(1.0, abs(ps)), (cd, ps)
+
+
+def test_cd_matches_sum_over_poles_other_state(small):
+    # a valence state n = 3 exercises O^{nm} rows that carry no core scaling
+    s = small
+    On3 = inputs.build_On(s["spec"], states=(3,))
+    W3 = o.w_imag_table(s["B"], s["D"], On3, s["xi"])[0]
+    for omega in (-0.9, -0.6, -0.45):   # away from eigenvalues: the quadrature cannot resolve |omega - eps_m| -> 0
+        cd = o.sigma_c_cd(s["B"], s["D"], On3[0], W3, s["eps"], s["spec"].n_occ, s["xi"], s["wxi"], omega, 1e-8)
+        ps = o.sigma_c_pole_sum(s["B"], s["D"], On3[0], s["eps"], s["spec"].n_occ, omega, 1e-8)
+        assert abs(cd.real - ps.real) < 1e-10 * max(1.0, abs(ps))
+
+
+def test_sigma_x_definition(small):
+    s = small
+    On = s["On"][0]
+    assert abs(o.sigma_x(On, s["spec"].n_occ) + sum(On[p, i] ** 2 for p in range(On.shape[0]) for i in range(5))) < 1e-13
+
+
+# --- Thiele continued fraction --------------------------------------------------------------------------
+
+def _rational_w(z, c, Om):
+    z = np.asarray(z, dtype=complex)
+    return sum(cj / (z * z - oj * oj) for cj, oj in zip(c, Om))
+
+
+def test_thiele_interpolates_its_nodes():
+    rng = np.random.default_rng(5)
+    z = np.concatenate([1j * np.geomspace(0.01, 50, 30), np.linspace(0.1, 9, 12) + 1e-3j])
+    W = _rational_w(z, rng.uniform(0.1, 1, 9), rng.uniform(0.3, 8, 9))
+    fit = o.thiele_greedy_fit(z, W, 24)
+    Tn = o.thiele_eval(fit.a, fit.z2, z[fit.nodes])
+    assert np.max(np.abs(Tn - W[fit.nodes]) / np.abs(W[fit.nodes])) < 1e-9
+
+
+def test_thiele_one_pole_exact_with_two_nodes():
+    c, Om = [-0.6], [1.3]
+    z = 1j * np.array([0.2, 0.9, 3.0])
+    fit = o.thiele_greedy_fit(z, _rational_w(z, c, Om), 2)
+    for zz in (0.5 + 0.01j, 4.0 + 1e-3j, 7j):
+        assert abs(o.thiele_eval(fit.a, fit.z2, zz) - _rational_w(zz, c, Om)) < 1e-13
+
+
+def test_thiele_three_poles_exact_with_six_nodes():
+    # sum of 3 poles in z^2 is rational of type [2/3] in z^2: exactly M = 6 reciprocal differences
+    c, Om = [-0.5, -0.2, -0.05], [0.8, 2.1, 5.0]
+    z = 1j * np.geomspace(0.05, 20, 40)
+    fit = o.thiele_greedy_fit(z, _rational_w(z, c, Om), 6)
+    probe = np.array([0.3 + 0.02j, 1.5 + 0.02j, 3.3 + 0.1j, 9.0 + 0.0j, 0.4j])
+    got = o.thiele_eval(fit.a, fit.z2, probe)
+    assert np.max(np.abs(got - _rational_w(probe, c, Om))) < 1e-10
+    # even M decays at infinity, odd M does not (Sec. 2.4)
+    assert abs(o.thiele_eval(fit.a, fit.z2, 1e6j)) < 1e-9
+    fit5 = o.thiele_greedy_fit(z, _rational_w(z, c, Om), 5)
+    assert abs(o.thiele_eval(fit5.a, fit5.z2, 1e6j)) > 1e-6
+
+
+def test_thiele_first_node_is_largest_w(small):
+    s = small
+    fit = o.thiele_greedy_fit(1j * s["xi"], s["Wim"][0][:, 2], 8)
+    assert fit.nodes[0] == int(np.argmax(np.abs(s["Wim"][0][:, 2])))
+    assert fit.nodes[0] == 0                                     # |W| is largest at the smallest xi
+    assert len(set(fit.nodes)) == 8
+
+
+def test_thiele_breakdown_on_duplicate_nodes():
+    z = 1j * np.array([0.5, 0.5, 0.5])
+    W = np.array([-1.0, -1.0, -1.0])
+    fit = o.thiele_greedy_fit(z, W, 3)
+    assert fit.breakdown and len(fit.nodes) < 3
+
+
+# --- quasiparticle solver -------------------------------------------------------------------------------
+
+def test_qp_fixed_point_linear_sigma():
+    eps_n, shift, alpha = -10.6, 0.05, 0.3
+    sig = lambda w: alpha * (w - eps_n) + 0.02
+    r = o.qp_solve(sig, eps_n, shift, np.linspace(-11, -10, 64))
+    expect = eps_n + (shift + 0.02) / (1 - alpha)
+    assert r.status == 0 and abs(r.e_qp - expect) < 1e-6 and abs(r.Z - 1 / (1 - alpha)) < 1e-6
+
+
+def test_qp_bisection_fallback():
+    # slope -3: the fixed-point map diverges, the bracketed root is (eps_n + 3 w*) / 4 with Z = 1/4
+    eps_n, ws = -10.6, -10.3
+    sig = lambda w: -3.0 * (w - ws)
+    r = o.qp_solve(sig, eps_n, 0.0, np.linspace(-11, -10, 64))
+    assert r.status == 1 and abs(r.e_qp - (eps_n + 3 * ws) / 4) < 1e-8 and abs(r.Z - 0.25) < 1e-6
+
+
+# --- CD-WAC against plain CD: the continuation error is measured, not pinned ---------------------------------
+
+def test_cdwac_near_real_points_span_residues(small):
+    s = small
+    zr = o.near_real_points(s["eps"], 5, s["eps"][0], 40)
+    assert len(zr) == 40 and zr[0].real == 0.0 and np.all(zr.imag == 1e-3)
+    assert abs(zr[-1].real - (abs(o.fermi_level(s["eps"], 5) - s["eps"][0]) + 0.5)) < 1e-12
+
+
+def test_cdwac_core_qp_close_to_cd(small):
+    s = small
+    grid = inputs.omega_grid(128)
+    P = o.Params(n_imag=100, n_real=40, pade_M=64, eta=1e-3)
+    cd = o.run_cd(s["B"], s["D"], s["On"], s["eps"], 5, [0], P, grid, with_sigma=False)
+    wac = o.run_cdwac(s["B"], s["D"], s["On"], s["eps"], 5, [0], P, grid, with_sigma=False)
+    e_cd, e_wac = cd["states"][0]["qp"].e_qp, wac["states"][0]["qp"].e_qp
+    assert cd["states"][0]["qp"].status == 0
+    assert abs(e_cd - e_wac) * 27211.386 < 0.01          # well inside 1 meV with 40 near-real points
