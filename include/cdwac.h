@@ -1,0 +1,173 @@
+/*
+ * cdwac.h -- C ABI of libcdwac.so: contour-deformation G0W0 self-energy of core levels with the analytic
+ * continuation of W (CD-WAC), on one NVIDIA GB300 (sm_103a).
+ *
+ * The calls follow the paper's problem statement (Panades-Barrueta & Golze, arXiv 2305.15955):
+ *   cdwac_build_W_imag  -- the wmatrix(F_Im) step of the G0W0 procedure (Sec. 3.4): Pi(i xi) (Eq. piriv),
+ *                          Lambda = (I - Pi)^-1 - I (Eq. bigLambda) and W_nm(i xi) (Eq. wriv) on the
+ *                          modified Gauss-Legendre grid (Sec. 4).
+ *   cdwac_fit_pade      -- the wmatrix(F_real) and AC steps (Secs. 3.3, 3.4): W_nm at near-real reference
+ *                          points, then one greedy Thiele continued fraction per (n, occupied m)
+ *                          (Eqs. pade, pre_rec, rec_eq; Sec. 3.2).
+ *   cdwac_sigma         -- Sigma^c_n(omega) = R_n(omega) - I_n(omega) (Eqs. In_term, Rn_term, ffact, cdselfe),
+ *                          with R_n from the continued fraction (CD-WAC) or from W built directly at every
+ *                          residue (plain CD).
+ *   cdwac_qp_solve      -- the quasiparticle equation e = eps_n + Re Sigma_n(e) - v^xc_n (Eq. qp_eq) by
+ *                          fixed-point iteration with a bracketed-bisection fallback.
+ *
+ * Conventions shared by every call
+ *   - Units are Hartree.  Complex numbers are stored as two doubles (re, im).
+ *   - Every pointer in cdwac_system, cdwac_pade and in the argument lists is DEVICE memory on the context's
+ *     device unless stated otherwise.  The caller owns all inputs and outputs; the context owns its scratch.
+ *   - Calls are asynchronous and ordered on the given CUDA stream (0 = legacy default stream).  The returned
+ *     status reports argument and launch errors.  Errors found on the device (a non-positive Cholesky pivot,
+ *     a singular complex pivot, a wait that ran out) are OR-ed into a device status word; cdwac_sync_status
+ *     waits for the stream and returns the first of them.  No call aborts, traps or waits without a bound.
+ *   - A context serves one device and one stream at a time; calls that overlap on two streams race on its
+ *     scratch.
+ */
+#ifndef CDWAC_H
+#define CDWAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CDWAC_OK = 0,
+  CDWAC_ERR_ARG = 1,               /* bad argument: sizes, null pointers, unsupported combination */
+  CDWAC_ERR_CUDA = 2,              /* a CUDA runtime call failed; cdwac_last_error has the text */
+  CDWAC_ERR_NOT_SPD = 3,           /* I - Pi(i xi) had a non-positive Cholesky pivot */
+  CDWAC_ERR_SINGULAR = 4,          /* I - Pi(z) had a (near) zero pivot in the complex LDL^T */
+  CDWAC_ERR_PADE_BREAKDOWN = 5,    /* a Thiele fit stopped early (informational; the fit is still usable) */
+  CDWAC_ERR_QP_NOT_CONVERGED = 6,  /* at least one state did not converge (per-state status has details) */
+  CDWAC_ERR_TIMEOUT = 7,           /* a bounded device wait gave up */
+  CDWAC_ERR_OOM = 8,               /* scratch allocation failed */
+  CDWAC_ERR_UNSUPPORTED = 9        /* operation not available on this device / build */
+} cdwac_status;
+
+typedef enum { CDWAC_F64 = 0, CDWAC_F32 = 1 } cdwac_dtype;
+
+/* Arithmetic of the W build.  FP64: every contraction in FP64 (parity path).  MIXED: Pi and the near-real
+ * Pi(z) as split-BF16 (hi/lo, three products) tcgen05 tensor-core contractions with FP32 accumulation; the
+ * Cholesky / LDL^T, the W projection, the Thiele fit and the residue sum stay FP64; the I_n quadrature terms
+ * are FP32 with FP64 partial sums. */
+typedef enum { CDWAC_PREC_FP64 = 0, CDWAC_PREC_MIXED = 1 } cdwac_precision;
+
+typedef struct cdwac_ctx cdwac_ctx;
+
+/* One closed-shell system in the RI-V representation (Sec. 2.2).
+ *   eps    [n_basis]                      ascending orbital energies; orbitals 0..n_occ-1 are occupied.
+ *   O_ia   [n_aux][n_occ * n_virt]        O^{ia}_P with column ia = i * n_virt + a (a counts virtuals from 0),
+ *                                         row-major, element type O_dtype; n_virt = n_basis - n_occ.
+ *   O_n    [n_states][n_aux][n_basis]     O^{n m}_P of each requested state n for every orbital m, O_dtype.
+ *   states [n_states] (int32)             orbital index n of each requested state.
+ * The O^{ia} block and the occupied-virtual entries of O_n must describe one tensor (O^{nm} = O^{mn}). */
+typedef struct {
+  int n_basis, n_occ, n_aux, n_states;
+  int O_dtype;                 /* cdwac_dtype */
+  const double* eps;
+  const void* O_ia;
+  const void* O_n;
+  const int* states;
+} cdwac_system;
+
+/* Method parameters (Secs. 3.2-3.4, 4).  cdwac_default_params fills the defaults noted here. */
+typedef struct {
+  int n_imag;          /* imaginary-axis Gauss-Legendre points (100) */
+  double omega0;       /* grid map xi = omega0 (1 + x) / (1 - x) (1.0 Ha) */
+  int n_real;          /* near-real reference points per state, generic set omega_G (40; 0 = imaginary only) */
+  double eta_ref;      /* imaginary part of the near-real points (1e-3 Ha) */
+  double real_margin;  /* near-real points span [0, |eps_F - eps_n| + real_margin] (0.5 Ha) */
+  double eta;          /* broadening i*eta in I_n and R_n (1e-3 Ha) */
+  int pade_M;          /* continued-fraction nodes per fit (64), at most n_imag + n_real and CDWAC_MAX_M */
+  int greedy_first;    /* first node: 0 = argmax |W|, 1 = argmax Re W, 2 = candidate 0 */
+  int greedy_crit;     /* later nodes: 0 = largest L1 error of the current convergent, 1 = smallest */
+  int precision;       /* cdwac_precision */
+} cdwac_params;
+
+#define CDWAC_MAX_M 256          /* largest continued fraction the fit kernel holds */
+#define CDWAC_MAX_CANDIDATES 512 /* largest n_imag + n_real */
+
+/* Thiele model of every (state n, occupied m): caller-owned device arrays sized from n_states, n_occ, M. */
+typedef struct {
+  int n_states, n_occ, M;      /* capacity the arrays were allocated for; M >= params.pade_M */
+  double* a;                   /* [n_states][n_occ][M][2] coefficients a_p */
+  double* z2;                  /* [n_states][n_occ][M][2] node values zt_p^2 */
+  int* nodes;                  /* [n_states][n_occ][M] candidate index of node p: 0..n_imag-1 = i xi_k,
+                                  n_imag + j = near-real point j */
+  int* n_used;                 /* [n_states][n_occ] nodes actually used (< pade_M after a breakdown) */
+} cdwac_pade;
+
+/* ---- context ------------------------------------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device` (makes it current for the calling thread).  *out is set to NULL
+ * on failure.  Returns CDWAC_ERR_UNSUPPORTED if the device is not compute capability 10.3. */
+cdwac_status cdwac_create(cdwac_ctx** out, int device);
+/* Frees the context's scratch.  Waits for nothing: the caller must have synchronised its streams. */
+void cdwac_destroy(cdwac_ctx* ctx);
+/* Text of the last error on this context (static storage owned by the context, never NULL). */
+const char* cdwac_last_error(const cdwac_ctx* ctx);
+/* Fills *p with the defaults listed in cdwac_params. */
+void cdwac_default_params(cdwac_params* p);
+/* Waits for `stream`, reads and clears the device status word; returns CDWAC_OK or the first device error. */
+cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream);
+/* Bytes of context scratch currently held (grows on demand, released by cdwac_destroy). */
+size_t cdwac_scratch_bytes(const cdwac_ctx* ctx);
+
+/* ---- the four steps ----------------------------------------------------------------------------------- */
+
+/* W_nm(i xi_k) on the imaginary grid: the wmatrix(F_Im) step (Sec. 3.4; Eqs. piriv, bigLambda, wriv).
+ *   xi, wxi  [n_imag]                        out: nodes xi_k (ascending) and quadrature weights of the
+ *                                            modified Gauss-Legendre grid (Sec. 4), Jacobian included.
+ *   W_imag   [n_states][n_imag][n_basis]     out: W^c_nm(i xi_k) for every m (real).
+ * Pi(i xi) = -4 sum_ia O^ia_P O^ia_Q D_ia / (xi^2 + D_ia^2) (spin factor 2), I - Pi is factorised by FP64
+ * Cholesky and W_nm = |L^-1 o_nm|^2 - |o_nm|^2 = o^T Lambda o.  Device error: CDWAC_ERR_NOT_SPD. */
+cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
+                                double* wxi, double* W_imag, void* stream);
+
+/* Near-real reference points, W there, and the greedy Thiele fits: the wmatrix(F_real) and AC steps.
+ *   xi, W_imag                               in: output of cdwac_build_W_imag with the same prm.
+ *   z_real   [n_states][n_real][2]           out (may be NULL): x_j + i eta_ref, x_j equidistant in
+ *                                            [0, |eps_F - eps_n| + real_margin], eps_F = (HOMO + LUMO) / 2.
+ *   W_real   [n_states][n_real][n_occ][2]    out (may be NULL): W_nm(z_j) for the occupied m.
+ *   pade                                     out: one fit per (n, occupied m) over the n_imag + n_real
+ *                                            candidates (greedy ordering of Sec. 3.2).
+ * Device error: CDWAC_ERR_SINGULAR.  A fit that breaks down keeps its first n_used nodes. */
+cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* W_imag, double* z_real, double* W_real, const cdwac_pade* pade,
+                            void* stream);
+
+/* Sigma^c_n(omega_j) = R_n - I_n (Eq. cdselfe without the static exchange).
+ *   xi, wxi, W_imag                          in: output of cdwac_build_W_imag.
+ *   pade                                     in: CD-WAC model, or NULL for plain CD (W built directly at each
+ *                                            residue |eps_m - omega| + i eta: one Pi(z) and one complex
+ *                                            LDL^T per residue, the O(N^5) route).
+ *   omega    [n_omega]                       in: real frequencies.  CD-WAC needs omega < eps_LUMO.
+ *   sigma    [n_states][n_omega][2]          out. */
+cdwac_status cdwac_sigma(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                         const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* omega,
+                         int n_omega, double* sigma, void* stream);
+
+/* Quasiparticle energies (Eq. qp_eq): e = eps_n + shift_n + Re Sigma^c_n(e), shift_n = Sigma^x_n - v^xc_n.
+ *   shift    [n_states]                      in (may be NULL = 0).
+ *   omega    [n_grid]                        in: bracketing grid of the bisection fallback.
+ *   e_qp, Z  [n_states]                      out: solution and renormalisation 1 / (1 - dRe Sigma/d omega)
+ *                                            (central difference, step 1e-5 Ha).
+ *   iters, qp_status [n_states] (int32)      out: fixed-point iterations; 0 = fixed point converged
+ *                                            (|e_k+1 - e_k| < tol), 1 = bracketed bisection, 2 = not converged.
+ * CD-WAC (pade != NULL) runs entirely on the device.  Plain CD (pade == NULL) drives one residue build per
+ * occupied orbital per iteration from the host and synchronises the stream between iterations. */
+cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
+                            const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                            int* iters, int* qp_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDWAC_H */

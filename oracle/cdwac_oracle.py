@@ -251,12 +251,13 @@ def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
     return ThieleFit(nodes=nodes, a=np.array(a, dtype=complex), z2=z2[np.array(nodes)], breakdown=breakdown)
 
 
-def near_real_points(eps, n_occ, eps_n, n_real, eta_ref=1e-3, margin=0.5):
+def near_real_points(eps, n_occ, eps_states, n_real, eta_ref=1e-3, margin=0.5):
     """Generic near-real reference set omega_G (Sec. 3.3): n_real equidistant points x_j + i eta_ref with
-    x_j spanning [0, |eps_F - eps_n| + margin], i.e. every residue |eps_m - omega| up to the Fermi level."""
+    x_j spanning [0, max_n |eps_F - eps_n| + margin], i.e. every residue |eps_m - omega| up to the Fermi level
+    of every requested state n (one set per system)."""
     if n_real == 0:
         return np.zeros(0, dtype=complex)
-    top = abs(fermi_level(eps, n_occ) - eps_n) + margin
+    top = max(abs(fermi_level(eps, n_occ) - e) for e in np.atleast_1d(eps_states)) + margin
     x = np.linspace(0.0, top, n_real)
     return x + 1j * eta_ref
 
@@ -404,10 +405,11 @@ def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=N
     occupied m, Sigma^c on omega_grid and the QP solution per state."""
     xi, wxi = imaginary_grid(params.n_imag, params.omega0)
     Wim = w_imag_table(B, D, On, xi)
-    out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "states": []}
+    zr = near_real_points(eps, n_occ, eps[list(states)], params.n_real, params.eta_ref, params.real_margin)
+    Wre_all = w_complex_table(B, D, On, zr, np.arange(n_occ)) if len(zr) else None
+    out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "z_real": zr, "states": []}
     for s, n in enumerate(states):
-        zr = near_real_points(eps, n_occ, eps[n], params.n_real, params.eta_ref, params.real_margin)
-        Wre = w_complex_table(B, D, On[s:s + 1], zr, np.arange(n_occ))[0] if len(zr) else np.zeros((0, n_occ), complex)
+        Wre = Wre_all[s] if len(zr) else np.zeros((0, n_occ), complex)
         model = fit_wac(Wim[s], Wre, xi, zr, n_occ, params.pade_M, params.greedy_first, params.greedy_criterion)
         sig = lambda w, s=s, model=model: sigma_c_wac(model, Wim[s], eps, n_occ, xi, wxi, w, params.eta)
         sh = 0.0 if shifts is None else shifts[s]

@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libcdwac.so (declared in include/cdwac.h).
+
+Argument marshalling only: PyTorch provides device memory and the current CUDA stream; every step of the
+computation runs in the library's CUDA kernels.  There is no CPU fallback: if the library or a GPU is missing,
+``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libcdwac.so")
+_lib = None
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOT_SPD, ERR_SINGULAR, ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED, ERR_TIMEOUT, ERR_OOM, \
+    ERR_UNSUPPORTED = range(10)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOT_SPD", "ERR_SINGULAR", "ERR_PADE_BREAKDOWN",
+                "ERR_QP_NOT_CONVERGED", "ERR_TIMEOUT", "ERR_OOM", "ERR_UNSUPPORTED"]
+F64, F32 = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+MAX_M = 256
+EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
+            "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve"]
+
+
+class CdwacError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("n_basis", ctypes.c_int), ("n_occ", ctypes.c_int), ("n_aux", ctypes.c_int),
+                ("n_states", ctypes.c_int), ("O_dtype", ctypes.c_int), ("eps", ctypes.c_void_p),
+                ("O_ia", ctypes.c_void_p), ("O_n", ctypes.c_void_p), ("states", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("n_imag", ctypes.c_int), ("omega0", ctypes.c_double), ("n_real", ctypes.c_int),
+                ("eta_ref", ctypes.c_double), ("real_margin", ctypes.c_double), ("eta", ctypes.c_double),
+                ("pade_M", ctypes.c_int), ("greedy_first", ctypes.c_int), ("greedy_crit", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+class _Pade(ctypes.Structure):
+    _fields_ = [("n_states", ctypes.c_int), ("n_occ", ctypes.c_int), ("M", ctypes.c_int),
+                ("a", ctypes.c_void_p), ("z2", ctypes.c_void_p), ("nodes", ctypes.c_void_p),
+                ("n_used", ctypes.c_void_p)]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load libcdwac.so (built by paper_2305_15955_gb300.build); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: run paper_2305_15955_gb300.build.build() first")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P = ctypes.c_void_p
+    lib.cdwac_create.argtypes = [ctypes.POINTER(P), ctypes.c_int]
+    lib.cdwac_destroy.argtypes = [P]
+    lib.cdwac_destroy.restype = None
+    lib.cdwac_last_error.argtypes = [P]
+    lib.cdwac_last_error.restype = ctypes.c_char_p
+    lib.cdwac_default_params.argtypes = [ctypes.POINTER(_Params)]
+    lib.cdwac_default_params.restype = None
+    lib.cdwac_sync_status.argtypes = [P, P]
+    lib.cdwac_scratch_bytes.argtypes = [P]
+    lib.cdwac_scratch_bytes.restype = ctypes.c_size_t
+    sysp, prmp, padep = ctypes.POINTER(_System), ctypes.POINTER(_Params), ctypes.POINTER(_Pade)
+    lib.cdwac_build_W_imag.argtypes = [P, sysp, prmp, P, P, P, P]
+    lib.cdwac_fit_pade.argtypes = [P, sysp, prmp, P, P, P, P, padep, P]
+    lib.cdwac_sigma.argtypes = [P, sysp, prmp, P, P, P, padep, P, ctypes.c_int, P, P]
+    lib.cdwac_qp_solve.argtypes = [P, sysp, prmp, P, P, P, padep, P, P, ctypes.c_int, ctypes.c_double,
+                                   ctypes.c_int, P, P, P, P, P]
+    _lib = lib
+    return lib
+
+
+@dataclasses.dataclass
+class Params:
+    """Mirror of cdwac_params (defaults as cdwac_default_params)."""
+    n_imag: int = 100
+    omega0: float = 1.0
+    n_real: int = 40
+    eta_ref: float = 1e-3
+    real_margin: float = 0.5
+    eta: float = 1e-3
+    pade_M: int = 64
+    greedy_first: int = 0
+    greedy_crit: int = 0
+    precision: int = PREC_FP64
+
+    def c(self) -> _Params:
+        return _Params(self.n_imag, self.omega0, self.n_real, self.eta_ref, self.real_margin, self.eta, self.pade_M,
+                       self.greedy_first, self.greedy_crit, self.precision)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class System:
+    """Device-resident system: eps [n_basis] f64, O_ia [n_aux, n_occ*n_virt], O_n [n_states, n_aux, n_basis]
+    (both f64 or both f32), states [n_states] int32."""
+
+    def __init__(self, eps, O_ia, O_n, states, n_occ, device="cuda"):
+        dev = torch.device(device)
+        self.eps = torch.as_tensor(eps, dtype=torch.float64).to(dev).contiguous()
+        self.O_ia = torch.as_tensor(O_ia).to(dev).contiguous()
+        self.O_n = torch.as_tensor(O_n).to(dev, dtype=self.O_ia.dtype).contiguous()
+        self.states = torch.as_tensor(np.asarray(states, dtype=np.int32)).to(dev).contiguous()
+        if self.O_ia.dtype not in (torch.float64, torch.float32):
+            raise ValueError("O must be float64 or float32")
+        self.n_basis = int(self.eps.numel())
+        self.n_occ = int(n_occ)
+        self.n_aux = int(self.O_ia.shape[0])
+        self.n_states = int(self.states.numel())
+        if tuple(self.O_ia.shape) != (self.n_aux, self.n_occ * (self.n_basis - self.n_occ)):
+            raise ValueError(f"O_ia shape {tuple(self.O_ia.shape)} does not match the sizes")
+        if tuple(self.O_n.shape) != (self.n_states, self.n_aux, self.n_basis):
+            raise ValueError(f"O_n shape {tuple(self.O_n.shape)} does not match the sizes")
+        self._c = _System(self.n_basis, self.n_occ, self.n_aux, self.n_states,
+                          F64 if self.O_ia.dtype == torch.float64 else F32, self.eps.data_ptr(),
+                          self.O_ia.data_ptr(), self.O_n.data_ptr(), self.states.data_ptr())
+
+    @property
+    def c(self):
+        return self._c
+
+
+@dataclasses.dataclass
+class PadeModel:
+    a: torch.Tensor        # [n_states, n_occ, M] complex128
+    z2: torch.Tensor       # [n_states, n_occ, M] complex128
+    nodes: torch.Tensor    # [n_states, n_occ, M] int32
+    n_used: torch.Tensor   # [n_states, n_occ] int32
+    z_real: torch.Tensor   # [n_states, n_real] complex128
+    W_real: torch.Tensor   # [n_states, n_real, n_occ] complex128
+    M: int
+
+    def c(self) -> _Pade:
+        ns, no, M = self.a.shape
+        return _Pade(ns, no, M, self.a.data_ptr(), self.z2.data_ptr(), self.nodes.data_ptr(), self.n_used.data_ptr())
+
+
+class Context:
+    """A libcdwac context bound to one CUDA device; calls run on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("libcdwac needs a CUDA device")
+        self.device = device
+        h = ctypes.c_void_p()
+        st = self.lib.cdwac_create(ctypes.byref(h), device)
+        if st != OK:
+            raise CdwacError(st, "cdwac_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            torch.cuda.synchronize(self.device)
+            self.lib.cdwac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _check(self, st):
+        if st != OK:
+            raise CdwacError(st, self.lib.cdwac_last_error(self.h).decode())
+
+    def sync_status(self, allow=(ERR_PADE_BREAKDOWN,)):
+        """Wait for the stream and raise on a device error (statuses in `allow` are returned, not raised)."""
+        st = self.lib.cdwac_sync_status(self.h, self._stream())
+        if st != OK and st not in allow:
+            raise CdwacError(st, self.lib.cdwac_last_error(self.h).decode())
+        return st
+
+    def scratch_bytes(self) -> int:
+        return int(self.lib.cdwac_scratch_bytes(self.h))
+
+    def _dev(self):
+        return torch.device("cuda", self.device)
+
+    def build_W_imag(self, system: System, params: Params, sync: bool = True):
+        dev = self._dev()
+        xi = torch.empty(params.n_imag, dtype=torch.float64, device=dev)
+        wxi = torch.empty_like(xi)
+        W = torch.empty(system.n_states, params.n_imag, system.n_basis, dtype=torch.float64, device=dev)
+        p = params.c()
+        self._check(self.lib.cdwac_build_W_imag(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi),
+                                                _ptr(wxi), _ptr(W), self._stream()))
+        if sync:
+            self.sync_status()
+        return xi, wxi, W
+
+    def alloc_pade(self, system: System, params: Params, M: int | None = None) -> PadeModel:
+        dev = self._dev()
+        M = params.pade_M if M is None else M
+        ns, no = system.n_states, system.n_occ
+        return PadeModel(a=torch.zeros(ns, no, M, dtype=torch.complex128, device=dev),
+                         z2=torch.zeros(ns, no, M, dtype=torch.complex128, device=dev),
+                         nodes=torch.full((ns, no, M), -1, dtype=torch.int32, device=dev),
+                         n_used=torch.zeros(ns, no, dtype=torch.int32, device=dev),
+                         z_real=torch.zeros(ns, max(params.n_real, 1), dtype=torch.complex128, device=dev),
+                         W_real=torch.zeros(ns, max(params.n_real, 1), no, dtype=torch.complex128, device=dev),
+                         M=M)
+
+    def fit_pade(self, system: System, params: Params, xi, W_imag, pade: PadeModel | None = None, sync=True):
+        pade = self.alloc_pade(system, params) if pade is None else pade
+        p = params.c()
+        pc = pade.c()
+        self._check(self.lib.cdwac_fit_pade(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(W_imag),
+                                            _ptr(pade.z_real), _ptr(pade.W_real), ctypes.byref(pc), self._stream()))
+        if sync:
+            self.sync_status()
+        return pade
+
+    def sigma(self, system: System, params: Params, xi, wxi, W_imag, pade: PadeModel | None, omega, sync=True):
+        dev = self._dev()
+        omega = torch.as_tensor(omega, dtype=torch.float64).to(dev).contiguous()
+        out = torch.empty(system.n_states, omega.numel(), dtype=torch.complex128, device=dev)
+        p = params.c()
+        pc = pade.c() if pade is not None else None
+        self._check(self.lib.cdwac_sigma(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(wxi),
+                                         _ptr(W_imag), ctypes.byref(pc) if pc is not None else None, _ptr(omega),
+                                         int(omega.numel()), _ptr(out), self._stream()))
+        if sync:
+            self.sync_status()
+        return out
+
+    def qp_solve(self, system: System, params: Params, xi, wxi, W_imag, pade: PadeModel | None, omega_grid,
+                 shift=None, tol=1e-7, max_iter=100, sync=True):
+        dev = self._dev()
+        grid = torch.as_tensor(omega_grid, dtype=torch.float64).to(dev).contiguous()
+        sh = None if shift is None else torch.as_tensor(shift, dtype=torch.float64).to(dev).contiguous()
+        ns = system.n_states
+        e = torch.empty(ns, dtype=torch.float64, device=dev)
+        Z = torch.empty_like(e)
+        it = torch.empty(ns, dtype=torch.int32, device=dev)
+        qs = torch.empty_like(it)
+        p = params.c()
+        pc = pade.c() if pade is not None else None
+        self._check(self.lib.cdwac_qp_solve(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(wxi),
+                                            _ptr(W_imag), ctypes.byref(pc) if pc is not None else None, _ptr(sh),
+                                            _ptr(grid), int(grid.numel()), float(tol), int(max_iter), _ptr(e),
+                                            _ptr(Z), _ptr(it), _ptr(qs), self._stream()))
+        if sync:
+            self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
+        return e, Z, it, qs

@@ -1,0 +1,496 @@
+// C ABI of libcdwac: argument checks, scratch layout and the stream-ordered sequence of kernels of each step
+// of the G0W0 procedure with CD and CD-WAC (Sec. 3.4).
+#include <stdarg.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "tc_pi.cuh"
+
+// ---- context and errors ----------------------------------------------------------------------------------
+
+cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...) {
+  if (ctx) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    ctx->last_error = buf;
+  }
+  return st;
+}
+
+cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->scratch_bytes) return CDWAC_OK;
+  if (ctx->scratch) {
+    CDWAC_CUDA_TRY(ctx, cudaDeviceSynchronize());
+    CDWAC_CUDA_TRY(ctx, cudaFree(ctx->scratch));
+    ctx->scratch = nullptr;
+    ctx->scratch_bytes = 0;
+  }
+  size_t want = bytes + (bytes >> 4);
+  cudaError_t e = cudaMalloc(&ctx->scratch, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    ctx->scratch = nullptr;
+    return set_error(ctx, CDWAC_ERR_OOM, "scratch allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  ctx->scratch_bytes = want;
+  return CDWAC_OK;
+}
+
+extern "C" {
+
+cdwac_status cdwac_create(cdwac_ctx** out, int device) {
+  if (!out) return CDWAC_ERR_ARG;
+  *out = nullptr;
+  cdwac_ctx* ctx = new cdwac_ctx();
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return CDWAC_ERR_CUDA;
+  }
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) {
+    delete ctx;
+    return CDWAC_ERR_CUDA;
+  }
+  if (!(p.major == 10 && p.minor == 3)) {
+    delete ctx;
+    return CDWAC_ERR_UNSUPPORTED;
+  }
+  ctx->num_sms = p.multiProcessorCount;
+  if (cudaMalloc(&ctx->d_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(ctx->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess) {
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return CDWAC_ERR_CUDA;
+  }
+  *out = ctx;
+  return CDWAC_OK;
+}
+
+void cdwac_destroy(cdwac_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  delete ctx;
+}
+
+const char* cdwac_last_error(const cdwac_ctx* ctx) { return ctx ? ctx->last_error.c_str() : "null context"; }
+
+size_t cdwac_scratch_bytes(const cdwac_ctx* ctx) { return ctx ? ctx->scratch_bytes : 0; }
+
+void cdwac_default_params(cdwac_params* p) {
+  if (!p) return;
+  p->n_imag = 100;
+  p->omega0 = 1.0;
+  p->n_real = 40;
+  p->eta_ref = 1e-3;
+  p->real_margin = 0.5;
+  p->eta = 1e-3;
+  p->pade_M = 64;
+  p->greedy_first = 0;
+  p->greedy_crit = 0;
+  p->precision = CDWAC_PREC_FP64;
+}
+
+cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream) {
+  if (!ctx) return CDWAC_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), st));
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  unsigned s = *ctx->h_status;
+  if (s & DEV_ERR_TIMEOUT) return set_error(ctx, CDWAC_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (s & DEV_ERR_NOT_SPD) return set_error(ctx, CDWAC_ERR_NOT_SPD, "I - Pi(i xi) is not positive definite");
+  if (s & DEV_ERR_SINGULAR) return set_error(ctx, CDWAC_ERR_SINGULAR, "I - Pi(z) has a vanishing pivot");
+  if (s & DEV_ERR_BOUNDS)
+    return set_error(ctx, CDWAC_ERR_ARG, "a frequency outside the range of the continuation (omega above the LUMO)");
+  if (s & DEV_INFO_QP_NOT_CONVERGED)
+    return set_error(ctx, CDWAC_ERR_QP_NOT_CONVERGED, "a quasiparticle equation did not converge");
+  if (s & DEV_INFO_PADE_BREAKDOWN)
+    return set_error(ctx, CDWAC_ERR_PADE_BREAKDOWN, "a Thiele fit stopped early (fit truncated)");
+  return CDWAC_OK;
+}
+
+}  // extern "C"
+
+// ---- shared pieces ------------------------------------------------------------------------------------------
+
+static cdwac_status check_system(cdwac_ctx* ctx, const cdwac_system* s, const cdwac_params* p) {
+  if (!ctx) return CDWAC_ERR_ARG;
+  if (!s || !p) return set_error(ctx, CDWAC_ERR_ARG, "null system or params");
+  if (s->n_basis < 2 || s->n_occ < 1 || s->n_occ >= s->n_basis || s->n_aux < 1 || s->n_states < 1)
+    return set_error(ctx, CDWAC_ERR_ARG, "bad sizes n_basis=%d n_occ=%d n_aux=%d n_states=%d", s->n_basis, s->n_occ,
+                     s->n_aux, s->n_states);
+  if (!s->eps || !s->O_ia || !s->O_n || !s->states) return set_error(ctx, CDWAC_ERR_ARG, "null system pointer");
+  if (s->O_dtype != CDWAC_F64 && s->O_dtype != CDWAC_F32) return set_error(ctx, CDWAC_ERR_ARG, "bad O_dtype");
+  if (p->n_imag < 1 || p->n_imag > 4096) return set_error(ctx, CDWAC_ERR_ARG, "n_imag out of range");
+  if (p->n_real < 0 || p->n_imag + p->n_real > CDWAC_MAX_CANDIDATES)
+    return set_error(ctx, CDWAC_ERR_ARG, "n_imag + n_real must be <= %d", CDWAC_MAX_CANDIDATES);
+  if (p->pade_M < 1 || p->pade_M > CDWAC_MAX_M) return set_error(ctx, CDWAC_ERR_ARG, "pade_M out of range");
+  if (!(p->omega0 > 0) || !(p->eta >= 0) || !(p->eta_ref > 0))
+    return set_error(ctx, CDWAC_ERR_ARG, "omega0, eta_ref must be > 0 and eta >= 0");
+  if (p->precision != CDWAC_PREC_FP64 && p->precision != CDWAC_PREC_MIXED)
+    return set_error(ctx, CDWAC_ERR_ARG, "bad precision");
+  if ((long)s->n_aux * s->n_aux > (1L << 31) * 16) return set_error(ctx, CDWAC_ERR_ARG, "n_aux too large");
+  return CDWAC_OK;
+}
+
+// Dense W build at one frequency: A = I - Pi(z) in `A`, factorised in place.
+template <class T>
+struct FactorScratch {
+  T* A;
+  T* dinv;
+  T* linv;
+  T* wpanel;
+  T* ywork;
+};
+
+template <class T>
+static size_t factor_scratch_bytes(int n, int n_cols) {
+  size_t el = (size_t)n * n + ldlt_scratch_elems<T>(n) + quadform_scratch_elems<T>(n, n_cols);
+  return el * sizeof(T) + 8 * 256;
+}
+
+template <class T>
+static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols) {
+  FactorScratch<T> f;
+  f.A = ar.take<T>((size_t)n * n);
+  int nblk = (n + 63) / 64;
+  f.dinv = ar.take<T>(n);
+  f.linv = ar.take<T>((size_t)nblk * 64 * 64);
+  f.wpanel = ar.take<T>((size_t)(nblk + 1) * 64 * 64);
+  f.ywork = ar.take<T>(quadform_scratch_elems<T>(n, n_cols));
+  return f;
+}
+
+// Mixed-precision operand planes of B = O^{ia}, built once per system and cached by pointer identity.
+struct MixedCache {
+  const void* src = nullptr;
+  int n_aux = 0;
+  long n_ov = 0;
+};
+
+extern "C" {
+
+cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
+                                double* wxi, double* W_imag, void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag) return set_error(ctx, CDWAC_ERR_ARG, "null output");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
+  const long n_ov = (long)n_occ * n_virt;
+  const int cols = sys->n_states * nb;
+  const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols) + 1024;
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov);
+  rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  Arena ar(ctx->scratch);
+  double* D = ar.take<double>(n_ov);
+  FactorScratch<double> f = carve_factor<double>(ar, n, cols);
+  void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+
+  if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
+  if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
+  if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+  for (int k = 0; k < prm->n_imag; ++k) {
+    if (mixed)
+      rc = tc_pi_imag(ctx, tcs, D, n, n_ov, xi + k, f.A, st);
+    else
+      rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, st);
+    if (rc) return rc;
+    if ((rc = ldlt_factor<double>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+    if ((rc = ldlt_quadform<double>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
+                                    sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st)))
+      return rc;
+  }
+  return CDWAC_OK;
+}
+
+cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* W_imag, double* z_real, double* W_real, const cdwac_pade* pade,
+                            void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !W_imag || !pade || !pade->a || !pade->z2 || !pade->nodes || !pade->n_used)
+    return set_error(ctx, CDWAC_ERR_ARG, "null input or pade array");
+  if (pade->n_states != sys->n_states || pade->n_occ != sys->n_occ || pade->M < prm->pade_M)
+    return set_error(ctx, CDWAC_ERR_ARG, "pade arrays sized for (%d, %d, %d), need (%d, %d, >= %d)", pade->n_states,
+                     pade->n_occ, pade->M, sys->n_states, sys->n_occ, prm->pade_M);
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
+  const long n_ov = (long)n_occ * n_virt;
+  const int nr = prm->n_real, ns = sys->n_states;
+  const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  size_t bytes = n_ov * sizeof(double) + 2 * sizeof(cplx) * (size_t)ns * nr * (n_occ + 1) + 4096;
+  if (nr > 0) bytes += factor_scratch_bytes<cplx>(n, ns * n_occ);
+  if (mixed && nr > 0) bytes += tc_pi_scratch_bytes(n, n_ov);
+  rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  Arena ar(ctx->scratch);
+  double* D = ar.take<double>(n_ov);
+  cplx* zr = z_real ? reinterpret_cast<cplx*>(z_real) : ar.take<cplx>((size_t)ns * nr + 1);
+  cplx* Wr = W_real ? reinterpret_cast<cplx*>(W_real) : ar.take<cplx>((size_t)ns * nr * n_occ + 1);
+  if (nr > 0) {
+    FactorScratch<cplx> f = carve_factor<cplx>(ar, n, ns * n_occ);
+    void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+    if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
+    if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, nr, prm->eta_ref, prm->real_margin,
+                                      reinterpret_cast<double*>(zr), st)))
+      return rc;
+    if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+    for (int j = 0; j < nr; ++j) {
+      if (mixed)
+        rc = tc_pi_complex(ctx, tcs, D, n, n_ov, zr + j, f.A, st);
+      else
+        rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zr + j, f.A, st);
+      if (rc) return rc;
+      if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      if ((rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns,
+                                    n_occ, Wr + (long)j * n_occ, (long)nr * n_occ, f.ywork, st)))
+        return rc;
+    }
+  }
+  return launch_thiele_fit(ctx, ns, n_occ, prm->n_imag, nr, xi, W_imag, nb, reinterpret_cast<const double*>(zr),
+                           reinterpret_cast<const double*>(Wr), prm, pade, st);
+}
+
+}  // extern "C"
+
+// Plain CD: Sigma[s][j] += f_m W_{n_s m}(|eps_m - omega_j| + i eta) for every residue, W built directly.
+__global__ static void add_residue_kernel(cplx* sigma, int n_omega, int j, int n_states, double f, const cplx* W,
+                                          long w_stride) {
+  int s = threadIdx.x;
+  if (s < n_states) {
+    cplx w = W[s * w_stride];
+    sigma[(long)s * n_omega + j] = sigma[(long)s * n_omega + j] + f * w;
+  }
+}
+
+__global__ static void set_z_kernel(cplx* z, double x, double eta) { z[0] = mkc(x, eta); }
+
+static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
+                                      const std::vector<double>& eps, const std::vector<double>& omega, double* sigma,
+                                      int n_omega_stride, int j_offset, cudaStream_t st) {
+  const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
+  const long n_ov = (long)n_occ * n_virt;
+  const int ns = sys->n_states;
+  const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<cplx>(n, ns) + sizeof(cplx) * (ns + 2) + 2048;
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov);
+  cdwac_status rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  Arena ar(ctx->scratch);
+  double* D = ar.take<double>(n_ov);
+  FactorScratch<cplx> f = carve_factor<cplx>(ar, n, ns);
+  cplx* zdev = ar.take<cplx>(1);
+  cplx* Wv = ar.take<cplx>(ns);
+  void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+  if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
+  if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+  for (size_t j = 0; j < omega.size(); ++j) {
+    const double w = omega[j];
+    for (int m = 0; m < nb; ++m) {
+      double th_occ = eps[m] > w ? 1.0 : (eps[m] < w ? 0.0 : 0.5);
+      double th_vir = w > eps[m] ? 1.0 : (w < eps[m] ? 0.0 : 0.5);
+      double fm = m < n_occ ? -th_occ : th_vir;
+      if (fm == 0.0) continue;
+      set_z_kernel<<<1, 1, 0, st>>>(zdev, fabs(eps[m] - w), prm->eta);
+      CDWAC_LAUNCH_CHECK(ctx);
+      if (mixed)
+        rc = tc_pi_complex(ctx, tcs, D, n, n_ov, zdev, f.A, st);
+      else
+        rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zdev, f.A, st);
+      if (rc) return rc;
+      if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      // column m of every state's O_n
+      if ((rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n,
+                                    sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + m)
+                                                              : (const void*)((const float*)sys->O_n + m),
+                                    sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1, f.ywork, st)))
+        return rc;
+      add_residue_kernel<<<1, 32 * ((ns + 31) / 32), 0, st>>>(reinterpret_cast<cplx*>(sigma), n_omega_stride,
+                                                              (int)j + j_offset, ns, fm, Wv, 1);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
+  }
+  return CDWAC_OK;
+}
+
+extern "C" {
+
+cdwac_status cdwac_sigma(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                         const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* omega,
+                         int n_omega, double* sigma, void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag || !omega || !sigma || n_omega < 0) return set_error(ctx, CDWAC_ERR_ARG, "bad sigma args");
+  if (pade && (pade->n_states != sys->n_states || pade->n_occ != sys->n_occ))
+    return set_error(ctx, CDWAC_ERR_ARG, "pade arrays do not match the system");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n_omega == 0) return CDWAC_OK;
+  if ((rc = launch_sigma_wac(ctx, sys, prm, xi, wxi, W_imag, pade, omega, n_omega, sigma, st))) return rc;
+  if (pade) return CDWAC_OK;
+  // plain CD: residues need the frequencies and eigenvalues on the host
+  std::vector<double> w(n_omega), e(sys->n_basis);
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(w.data(), omega, sizeof(double) * n_omega, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(e.data(), sys->eps, sizeof(double) * sys->n_basis, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return plain_cd_residues(ctx, sys, prm, e, w, sigma, n_omega, 0, st);
+}
+
+// Plain-CD quasiparticle solve for one state: host-driven fixed point, one Sigma evaluation per iteration.
+static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, const cdwac_params* prm,
+                                      const double* xi, const double* wxi, const double* W_imag_s,
+                                      const std::vector<double>& eps, double en, double sh,
+                                      const std::vector<double>& grid, double tol, int max_iter, double* out_e,
+                                      double* out_z, int* out_it, int* out_st, double* dsig, cudaStream_t st) {
+  auto resig = [&](double w, double* val) -> cdwac_status {
+    cdwac_status r;
+    std::vector<double> wv(1, w);
+    // omega must be on the device for the I term: reuse dsig[2..] as the frequency slot
+    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(dsig + 2, &w, sizeof(double), cudaMemcpyHostToDevice, st));
+    if ((r = launch_sigma_wac(ctx, sub, prm, xi, wxi, W_imag_s, nullptr, dsig + 2, 1, dsig, st))) return r;
+    if ((r = plain_cd_residues(ctx, sub, prm, eps, wv, dsig, 1, 0, st))) return r;
+    double h[2];
+    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(h, dsig, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    *val = h[0];
+    return CDWAC_OK;
+  };
+  const double hstep = 1e-5;
+  auto zfac = [&](double e, double* z) -> cdwac_status {
+    double a, b;
+    cdwac_status r;
+    if ((r = resig(e + hstep, &a))) return r;
+    if ((r = resig(e - hstep, &b))) return r;
+    *z = 1.0 / (1.0 - (a - b) / (2.0 * hstep));
+    return CDWAC_OK;
+  };
+  cdwac_status rc;
+  double e = en, e_new = en, s;
+  for (int it = 1; it <= max_iter; ++it) {
+    if ((rc = resig(e, &s))) return rc;
+    e_new = en + sh + s;
+    if (fabs(e_new - e) < tol) {
+      *out_e = e_new;
+      *out_it = it;
+      *out_st = 0;
+      return zfac(e_new, out_z);
+    }
+    e = e_new;
+  }
+  *out_it = max_iter;
+  bool found = false;
+  double be = 0, bz = 0;
+  auto f = [&](double w, double* v) -> cdwac_status {
+    double sv;
+    cdwac_status r = resig(w, &sv);
+    *v = w - en - sh - sv;
+    return r;
+  };
+  double fprev;
+  if ((rc = f(grid[0], &fprev))) return rc;
+  for (size_t j = 0; j + 1 < grid.size(); ++j) {
+    double fnext;
+    if ((rc = f(grid[j + 1], &fnext))) return rc;
+    if (fprev == 0.0 || fprev * fnext < 0.0) {
+      double lo = grid[j], hi = grid[j + 1], flo = fprev;
+      for (int b = 0; b < 200 && hi - lo > 1e-9; ++b) {
+        double mid = 0.5 * (lo + hi), fm;
+        if ((rc = f(mid, &fm))) return rc;
+        if (fm * flo <= 0.0) {
+          hi = mid;
+        } else {
+          lo = mid;
+          flo = fm;
+        }
+      }
+      double r = 0.5 * (lo + hi), fr;
+      if ((rc = f(r, &fr))) return rc;
+      if (fabs(fr) < 1e-6) {
+        double zr;
+        if ((rc = zfac(r, &zr))) return rc;
+        if (zr > 0.0 && zr <= 1.0 && (!found || zr > bz)) {
+          found = true;
+          be = r;
+          bz = zr;
+        }
+      }
+    }
+    fprev = fnext;
+  }
+  if (found) {
+    *out_e = be;
+    *out_z = bz;
+    *out_st = 1;
+    return CDWAC_OK;
+  }
+  *out_e = e;
+  *out_st = 2;
+  return zfac(e, out_z);
+}
+
+cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
+                            const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                            int* iters, int* qp_status, void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag || !omega || n_grid < 2 || !e_qp || !Z || !iters || !qp_status || max_iter < 1 ||
+      !(tol > 0))
+    return set_error(ctx, CDWAC_ERR_ARG, "bad qp_solve args");
+  if (pade && (pade->n_states != sys->n_states || pade->n_occ != sys->n_occ))
+    return set_error(ctx, CDWAC_ERR_ARG, "pade arrays do not match the system");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  if (pade)
+    return launch_qp_wac(ctx, sys, prm, xi, wxi, W_imag, pade, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters,
+                         qp_status, st);
+  // plain CD: host-driven iteration per state
+  const int ns = sys->n_states, nb = sys->n_basis;
+  std::vector<double> e(nb), grid(n_grid), sh(ns, 0.0);
+  std::vector<int> states(ns);
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(e.data(), sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(grid.data(), omega, sizeof(double) * n_grid, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(states.data(), sys->states, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+  if (shift) CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(sh.data(), shift, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  double* dsig = nullptr;
+  CDWAC_CUDA_TRY(ctx, cudaMalloc(&dsig, 4 * sizeof(double)));
+  std::vector<double> he(ns), hz(ns);
+  std::vector<int> hit(ns), hst(ns);
+  for (int s = 0; s < ns && rc == CDWAC_OK; ++s) {
+    cdwac_system sub = *sys;
+    sub.n_states = 1;
+    sub.states = sys->states + s;
+    sub.O_n = sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + (long)s * sys->n_aux * nb)
+                                        : (const void*)((const float*)sys->O_n + (long)s * sys->n_aux * nb);
+    rc = qp_plain_cd_state(ctx, &sub, prm, xi, wxi, W_imag + (long)s * prm->n_imag * nb, e, e[states[s]], sh[s],
+                           grid, tol, max_iter, &he[s], &hz[s], &hit[s], &hst[s], dsig, st);
+  }
+  cudaFree(dsig);
+  if (rc) return rc;
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(e_qp, he.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(Z, hz.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(iters, hit.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(qp_status, hst.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return CDWAC_OK;
+}
+
+}  // extern "C"

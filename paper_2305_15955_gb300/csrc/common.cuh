@@ -1,0 +1,165 @@
+// Shared definitions of libcdwac: the context, error plumbing, the complex scalar, launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/cdwac.h"
+
+// Device status bits (OR-ed into the context's status word by kernels).
+enum : unsigned {
+  DEV_ERR_NOT_SPD = 1u << 0,
+  DEV_ERR_SINGULAR = 1u << 1,
+  DEV_INFO_PADE_BREAKDOWN = 1u << 2,
+  DEV_INFO_QP_NOT_CONVERGED = 1u << 3,
+  DEV_ERR_TIMEOUT = 1u << 4,
+  DEV_ERR_BOUNDS = 1u << 5,
+};
+
+struct cdwac_ctx {
+  int device = 0;
+  int num_sms = 0;
+  unsigned* d_status = nullptr;     // device status word
+  unsigned* h_status = nullptr;     // pinned mirror
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  std::string last_error;
+};
+
+// Bump allocator over the context scratch; every region is 256-byte aligned.
+struct Arena {
+  char* base;
+  size_t off = 0;
+  explicit Arena(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes);
+cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...);
+
+#define CDWAC_CUDA_TRY(ctx, expr)                                                                 \
+  do {                                                                                            \
+    cudaError_t e_ = (expr);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return set_error((ctx), CDWAC_ERR_CUDA, "%s:%d %s: %s", __FILE__, __LINE__, #expr,         \
+                       cudaGetErrorString(e_));                                                   \
+  } while (0)
+
+#define CDWAC_LAUNCH_CHECK(ctx) CDWAC_CUDA_TRY(ctx, cudaGetLastError())
+
+// ---- complex scalar (re, im) with the operations the kernels need ------------------------------------------
+struct cplx {
+  double x, y;
+};
+__host__ __device__ inline cplx mkc(double x, double y) { return cplx{x, y}; }
+__host__ __device__ inline cplx operator+(cplx a, cplx b) { return {a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cplx operator-(cplx a, cplx b) { return {a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cplx operator*(cplx a, cplx b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__host__ __device__ inline cplx operator*(double s, cplx a) { return {s * a.x, s * a.y}; }
+// Smith's division (R. L. Smith, CACM 5(8), 1962): scales by the larger component to avoid overflow.
+__host__ __device__ inline cplx operator/(cplx a, cplx b) {
+  double br = fabs(b.x), bi = fabs(b.y);
+  if (br >= bi) {
+    if (br == 0.0 && bi == 0.0) return {a.x / br, a.y / br};
+    double rat = b.y / b.x, scl = 1.0 / (b.x + b.y * rat);
+    return {(a.x + a.y * rat) * scl, (a.y - a.x * rat) * scl};
+  }
+  double rat = b.x / b.y, scl = 1.0 / (b.y + b.x * rat);
+  return {(a.x * rat + a.y) * scl, (a.y * rat - a.x) * scl};
+}
+__host__ __device__ inline bool finite_c(cplx a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Scalar traits so that one LDL^T / solve template serves the real (imaginary axis) and complex (near-real
+// and residue) cases.
+template <class T>
+struct Num;
+template <>
+struct Num<double> {
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double one() { return 1.0; }
+  __device__ static double fma_(double a, double b, double c) { return fma(a, b, c); }   // a*b + c
+  __device__ static double fms(double a, double b, double c) { return fma(-a, b, c); }   // c - a*b
+  __device__ static double mul(double a, double b) { return a * b; }
+  __device__ static double div(double a, double b) { return a / b; }
+  __device__ static double sub(double a, double b) { return a - b; }
+  __device__ static double add(double a, double b) { return a + b; }
+  __device__ static double re(double a) { return a; }
+  __device__ static double mag(double a) { return fabs(a); }
+};
+template <>
+struct Num<cplx> {
+  __host__ __device__ static cplx zero() { return {0.0, 0.0}; }
+  __host__ __device__ static cplx one() { return {1.0, 0.0}; }
+  __device__ static cplx fma_(cplx a, cplx b, cplx c) {
+    return {fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y))};
+  }
+  __device__ static cplx fms(cplx a, cplx b, cplx c) {
+    return {fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y))};
+  }
+  __device__ static cplx mul(cplx a, cplx b) { return a * b; }
+  __device__ static cplx div(cplx a, cplx b) { return a / b; }
+  __device__ static cplx sub(cplx a, cplx b) { return a - b; }
+  __device__ static cplx add(cplx a, cplx b) { return a + b; }
+  __device__ static double re(cplx a) { return a.x; }
+  __device__ static double mag(cplx a) { return hypot(a.x, a.y); }
+};
+
+__device__ inline void raise_status(unsigned* status, unsigned bit) {
+  if (status) atomicOr(status, bit);
+}
+
+inline int ceil_div(long a, long b) { return int((a + b - 1) / b); }
+
+// ---- entry points of the individual translation units (host side, stream ordered) -----------------------
+// grid.cu
+cdwac_status launch_gauss_legendre(cdwac_ctx* ctx, int n, double omega0, double* xi, double* wxi,
+                                   cudaStream_t st);
+// pi_simt.cu: A = I - Pi(z) (lower triangle), FP64 SIMT.  B is [n_aux][n_ov] (f64 or f32).
+// xi (or z) is read on the device from xi_dev[0] (z_dev[0]), so that host code never waits for it.
+cdwac_status launch_pi_imag_fp64(cdwac_ctx* ctx, const void* B, int dtype, const double* D, int n_aux, int n_ov,
+                                 const double* xi_dev, double* A, cudaStream_t st);
+cdwac_status launch_pi_complex_fp64(cdwac_ctx* ctx, const void* B, int dtype, const double* D, int n_aux,
+                                    int n_ov, const cplx* z_dev, cplx* A, cudaStream_t st);
+cdwac_status launch_transition_energies(cdwac_ctx* ctx, const double* eps, int n_occ, int n_virt, double* D,
+                                        cudaStream_t st);
+// ldlt.cu
+template <class T>
+cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st);
+template <class T>
+size_t ldlt_scratch_elems(int n);
+// W[s][m] = sum_P y_Pm^2 / d_P - sum_P o_Pm^2, y = L^{-1} o, for states s < n_states and columns
+// m < cols_per_state; o_Pm of state s is O[s * o_state_stride + P * ld_o + m] (element type dtype) and the
+// result goes to W_out[s * w_state_stride + m].
+template <class T>
+cdwac_status ldlt_quadform(cdwac_ctx* ctx, const T* L, const T* dinv, const T* linv_blocks, int n, const void* O,
+                           int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, T* W_out,
+                           long w_state_stride, T* ywork, cudaStream_t st);
+template <class T>
+size_t quadform_scratch_elems(int n, int n_cols);
+// thiele.cu
+cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_imag, int n_real, const double* xi,
+                               const double* W_imag, int n_basis, const double* z_real, const double* W_real,
+                               const cdwac_params* prm, const cdwac_pade* pade, cudaStream_t st);
+cdwac_status launch_near_real_points(cdwac_ctx* ctx, const double* eps, int n_occ, const int* states,
+                                     int n_states, int n_real, double eta_ref, double margin, double* z_real,
+                                     cudaStream_t st);
+// sigma.cu
+cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                              const double* wxi, const double* W_imag, const cdwac_pade* pade,
+                              const double* omega, int n_omega, double* sigma, cudaStream_t st);
+cdwac_status launch_sigma_I_only(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
+                                 const double* xi, const double* wxi, const double* W_imag, const double* omega,
+                                 int n_omega, double* sigma, cudaStream_t st);
+cdwac_status launch_qp_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                           const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
+                           const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                           int* iters, int* qp_status, cudaStream_t st);

@@ -1,0 +1,373 @@
+// Square-root-free Cholesky factorisation A = L D L^T of I - Pi (Eq. bigLambda) and the quadratic forms
+// W_nm = o^T [(I - Pi)^-1 - I] o = sum_P y_P^2 / d_P - sum_P o_P^2,  y = L^-1 o   (Eq. wriv),
+// in FP64, for real symmetric positive definite A (imaginary axis, Cholesky without square roots) and for
+// complex symmetric A (near-real points and residues; no conjugation, no pivoting).
+//
+// Blocked right-looking factorisation with NB = 64 column blocks, three launches per block step:
+//   diag  : one CTA factors the NB x NB diagonal block in shared memory and inverts its unit-lower L_kk;
+//   panel : rows below: W_ik = A_ik L_kk^-T, L_ik = W_ik D_k^-1 (W_ik kept in a panel buffer);
+//   update: trailing lower triangle A_ij -= W_ik L_jk^T.
+// Only the lower triangle of A is read or written.  A non-positive (real) or vanishing (complex) pivot sets
+// CDWAC_ERR_NOT_SPD / CDWAC_ERR_SINGULAR in the status word and the factorisation continues with a unit pivot,
+// so no NaN reaches later kernels.
+#include "common.cuh"
+
+__device__ inline double mkT(double v, double*) { return v; }
+__device__ inline cplx mkT(double v, cplx*) { return mkc(v, 0.0); }
+
+namespace {
+
+constexpr int NB = 64;
+constexpr int TK = 16;
+constexpr int TP = 64 + 1;
+
+template <class T>
+__device__ inline T ld_as(const void* p, int dtype, long idx);
+template <>
+__device__ inline double ld_as<double>(const void* p, int dtype, long idx) {
+  return dtype == CDWAC_F64 ? ((const double*)p)[idx] : (double)((const float*)p)[idx];
+}
+
+__device__ inline bool bad_pivot(double d) { return !(d > 0.0); }
+__device__ inline bool bad_pivot(cplx d) { return !(hypot(d.x, d.y) > 1e-300); }
+__device__ inline unsigned pivot_err(double) { return DEV_ERR_NOT_SPD; }
+__device__ inline unsigned pivot_err(cplx) { return DEV_ERR_SINGULAR; }
+
+// ---- diagonal block --------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv, T* linv, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);            // [NB][NB]
+  T* X = S + NB * NB;                                // [NB][NB] inverse of unit-lower L_kk
+  using N = Num<T>;
+  const int nb = min(NB, n - k0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int i = e / NB, j = e % NB;
+    S[e] = (i < nb && j <= i) ? A[(long)(k0 + i) * n + (k0 + j)] : (i == j ? N::one() : N::zero());
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    T d = S[j * NB + j];
+    const bool bad = bad_pivot(d);                   // same value in every thread
+    __syncthreads();                                 // every thread has read the pivot
+    if (bad) {
+      d = N::one();
+      if (tid == 0) {
+        raise_status(status, pivot_err(S[j * NB + j]));
+        S[j * NB + j] = N::one();
+      }
+      __syncthreads();
+    }
+    // a_ik -= a_ij a_kj / d for j < k <= i < nb  (uses the unscaled column j)
+    const int m = nb - j - 1;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) S[i * NB + k] = N::fms(N::div(S[i * NB + j], d), S[k * NB + j], S[i * NB + k]);
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i * NB + j] = N::div(S[i * NB + j], d);
+    __syncthreads();
+  }
+  // X = L_kk^{-1}, column c by thread c: X[c][c] = 1, X[i][c] = -sum_{c <= t < i} L[i][t] X[t][c]
+  for (int c = tid; c < NB; c += blockDim.x) {
+    for (int i = 0; i < NB; ++i) X[i * NB + c] = N::zero();
+    if (c < nb) {
+      X[c * NB + c] = N::one();
+      for (int i = c + 1; i < nb; ++i) {
+        T s = N::zero();
+        for (int t = c; t < i; ++t) s = N::fma_(S[i * NB + t], X[t * NB + c], s);
+        X[i * NB + c] = N::sub(N::zero(), s);
+      }
+    }
+  }
+  __syncthreads();
+  const int kb = k0 / NB;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    int i = e / NB, j = e % NB;
+    linv[(long)kb * NB * NB + e] = X[e];
+    if (i < nb && j <= i) A[(long)(k0 + i) * n + (k0 + j)] = S[e];   // diagonal holds d_i
+  }
+  for (int i = tid; i < nb; i += blockDim.x) dinv[k0 + i] = N::div(N::one(), S[i * NB + i]);
+}
+
+// ---- panel: W_i = A_i L_kk^-T, L_i = W_i D^-1 for the 64-row block of rows below the diagonal block ------
+template <class T>
+__global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int k0, const T* dinv, const T* linv, T* wpanel) {
+  __shared__ T Xs[TK][TP];       // chunk of L_kk^-1 rows [j][c]: Xs[c - c0][j]
+  __shared__ T As[TK][TP];       // chunk of A panel: As[c - c0][r]
+  using N = Num<T>;
+  const int nb = min(NB, n - k0);
+  const int r0 = k0 + NB + blockIdx.x * 64;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int kb = k0 / NB;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = N::zero();
+  for (int c0 = 0; c0 < nb; c0 += TK) {
+    for (int e = tid; e < TK * 64; e += 256) {
+      int cc = e % TK, r = e / TK;
+      int c = c0 + cc;
+      int row = r0 + r;
+      As[cc][r] = (row < n && c < nb) ? A[(long)row * n + k0 + c] : N::zero();
+      // (L^-T)[c][j] = Linv[j][c]
+      Xs[cc][r] = (c < nb) ? linv[(long)kb * NB * NB + (long)r * NB + c] : N::zero();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TK; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[q][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Xs[q][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = N::fma_(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int row = r0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int c = tx * 4 + j;
+      if (row < n && c < nb) {
+        wpanel[(long)row * NB + c] = acc[i][j];
+        A[(long)row * n + k0 + c] = N::mul(acc[i][j], dinv[k0 + c]);
+      }
+    }
+  }
+}
+
+__device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
+  int t = int((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+  while ((t + 1) * (t + 2) / 2 <= b) ++t;
+  while (t * (t + 1) / 2 > b) --t;
+  ti = t;
+  tj = b - t * (t + 1) / 2;
+}
+
+// ---- trailing update: A_ij -= W_i L_j^T over the lower triangle of rows/cols >= k1 -----------------------
+template <class T>
+__global__ void __launch_bounds__(256) update_kernel(T* A, int n, int k0, const T* wpanel) {
+  __shared__ T Ws[TK][TP];
+  __shared__ T Ls[TK][TP];
+  using N = Num<T>;
+  const int nb = min(NB, n - k0);
+  const int k1 = k0 + NB;
+  int ti, tj;
+  lower_tile_coords(blockIdx.x, ti, tj);
+  const int row0 = k1 + ti * 64, col0 = k1 + tj * 64;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = N::zero();
+  for (int c0 = 0; c0 < nb; c0 += TK) {
+    for (int e = tid; e < TK * 64; e += 256) {
+      int cc = e % TK, r = e / TK;
+      int c = c0 + cc;
+      int ra = row0 + r, rb = col0 + r;
+      Ws[cc][r] = (ra < n && c < nb) ? wpanel[(long)ra * NB + c] : N::zero();
+      Ls[cc][r] = (rb < n && c < nb) ? A[(long)rb * n + k0 + c] : N::zero();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TK; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Ws[q][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Ls[q][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = N::fma_(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    int P = row0 + ty * 4 + i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int Q = col0 + tx * 4 + j;
+      if (P < n && Q <= P) {
+        long idx = (long)P * n + Q;
+        A[idx] = N::sub(A[idx], acc[i][j]);
+      }
+    }
+  }
+}
+
+// ---- quadratic forms through forward substitution -----------------------------------------------------------
+// One CTA owns QC columns of O and walks all 64-row blocks: t_i = o_i - L_i,<i y_<i, y_i = L_ii^-1 t_i.
+constexpr int QC = 8;    // columns per CTA
+constexpr int QK = 16;   // K chunk of the off-diagonal product
+
+template <class T>
+__global__ void __launch_bounds__(256) quadform_kernel(const T* __restrict__ L, const T* __restrict__ dinv,
+                                                       const T* __restrict__ linv, int n, const void* O, int dtype,
+                                                       long o_state_stride, long ld_o, int cols_per_state,
+                                                       int n_cols, T* ywork, T* W_out, long w_state_stride) {
+  __shared__ T Ls[64][QK + 1];
+  __shared__ T Ys[QK][QC];
+  __shared__ T Ts[64][QC];
+  __shared__ T red[256];
+  __shared__ double ored[256];
+  using N = Num<T>;
+  const int tid = threadIdx.x;
+  const int c_base = blockIdx.x * QC;          // first column (relative to m0) of this CTA
+  const int npad = ((n + 63) / 64) * 64;
+  T* Y = ywork + (long)blockIdx.x * npad * QC; // this CTA's y, [npad][QC]
+  const int r = tid / 4, cg = tid % 4;          // thread owns row r of the block, columns 2cg, 2cg+1
+  T wacc[2] = {N::zero(), N::zero()};
+  double oacc[2] = {0.0, 0.0};
+  const int nblk = (n + 63) / 64;
+  for (int ib = 0; ib < nblk; ++ib) {
+    const int i0 = ib * 64;
+    T t[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int c = cg * 2 + u, col = c_base + c;
+      int row = i0 + r;
+      if (row < n && col < n_cols) {
+        const int cs = col / cols_per_state, cm = col % cols_per_state;
+        double ov = ld_as<double>(O, dtype, cs * o_state_stride + (long)row * ld_o + cm);
+        oacc[u] += ov * ov;
+        t[u] = mkT(ov, (T*)nullptr);
+      } else {
+        t[u] = N::zero();
+      }
+    }
+    for (int k0 = 0; k0 < i0; k0 += QK) {
+      for (int e = tid; e < 64 * QK; e += 256) {
+        int rr = e / QK, kk = e % QK;
+        int row = i0 + rr, col = k0 + kk;
+        Ls[rr][kk] = (row < n) ? L[(long)row * n + col] : N::zero();
+      }
+      for (int e = tid; e < QK * QC; e += 256) {
+        int kk = e / QC, c = e % QC;
+        Ys[kk][c] = Y[(long)(k0 + kk) * QC + c];
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < QK; ++kk) {
+        T lv = Ls[r][kk];
+        t[0] = N::fms(lv, Ys[kk][cg * 2 + 0], t[0]);
+        t[1] = N::fms(lv, Ys[kk][cg * 2 + 1], t[1]);
+      }
+      __syncthreads();
+    }
+    Ts[r][cg * 2 + 0] = t[0];
+    Ts[r][cg * 2 + 1] = t[1];
+    __syncthreads();
+    // y_i = Linv_ii t_i  (unit lower 64 x 64)
+    const T* X = linv + (long)ib * 64 * 64;
+    T y[2] = {N::zero(), N::zero()};
+    for (int c = 0; c <= r; ++c) {
+      T xv = X[r * 64 + c];
+      y[0] = N::fma_(xv, Ts[c][cg * 2 + 0], y[0]);
+      y[1] = N::fma_(xv, Ts[c][cg * 2 + 1], y[1]);
+    }
+    const int row = i0 + r;
+    if (row < n) {
+      T di = dinv[row];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        Y[(long)row * QC + cg * 2 + u] = y[u];
+        wacc[u] = N::fma_(N::mul(y[u], y[u]), di, wacc[u]);
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) Y[(long)row * QC + cg * 2 + u] = N::zero();
+    }
+    __syncthreads();
+  }
+  // reduce over the 64 rows for each of the QC columns: thread (r, cg) holds columns 2cg, 2cg+1
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    red[tid] = wacc[u];
+    ored[tid] = oacc[u];
+    __syncthreads();
+    for (int s = 128; s >= 4; s >>= 1) {   // tid = 4 r + cg: partners differ in r
+      if (tid < s) {
+        red[tid] = N::add(red[tid], red[tid + s]);
+        ored[tid] += ored[tid + s];
+      }
+      __syncthreads();
+    }
+    if (tid < 4) {
+      int col = c_base + tid * 2 + u;
+      if (col < n_cols) {
+        const int cs = col / cols_per_state, cm = col % cols_per_state;
+        W_out[cs * w_state_stride + cm] = N::sub(red[tid], mkT(ored[tid], (T*)nullptr));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+template <class T>
+size_t ldlt_scratch_elems(int n) {
+  int nblk = (n + NB - 1) / NB;
+  return (size_t)n /*dinv*/ + (size_t)nblk * NB * NB /*linv*/ + (size_t)(nblk + 1) * NB * NB /*wpanel rows*/;
+}
+
+template <class T>
+cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st) {
+  const size_t dsmem = 2 * NB * NB * sizeof(T);
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+  for (int k0 = 0; k0 < n; k0 += NB) {
+    diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0, dinv, linv_blocks, ctx->d_status);
+    CDWAC_LAUNCH_CHECK(ctx);
+    int rest = n - (k0 + NB);
+    if (rest <= 0) break;
+    int rblk = ceil_div(rest, 64);
+    panel_kernel<T><<<rblk, 256, 0, st>>>(A, n, k0, dinv, linv_blocks, wpanel);
+    CDWAC_LAUNCH_CHECK(ctx);
+    update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel);
+    CDWAC_LAUNCH_CHECK(ctx);
+  }
+  return CDWAC_OK;
+}
+
+template <class T>
+size_t quadform_scratch_elems(int n, int n_cols) {
+  int blocks = (n_cols + QC - 1) / QC;
+  int npad = ((n + 63) / 64) * 64;
+  return (size_t)blocks * npad * QC;
+}
+
+template <class T>
+cdwac_status ldlt_quadform(cdwac_ctx* ctx, const T* L, const T* dinv, const T* linv_blocks, int n, const void* O,
+                           int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, T* W_out,
+                           long w_state_stride, T* ywork, cudaStream_t st) {
+  const int n_cols = n_states * cols_per_state;
+  if (n_cols <= 0) return CDWAC_OK;
+  int blocks = ceil_div(n_cols, QC);
+  quadform_kernel<T><<<blocks, 256, 0, st>>>(L, dinv, linv_blocks, n, O, dtype, o_state_stride, ld_o,
+                                             cols_per_state, n_cols, ywork, W_out, w_state_stride);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+template size_t ldlt_scratch_elems<double>(int);
+template size_t ldlt_scratch_elems<cplx>(int);
+template size_t quadform_scratch_elems<double>(int, int);
+template size_t quadform_scratch_elems<cplx>(int, int);
+template cdwac_status ldlt_factor<double>(cdwac_ctx*, double*, int, double*, double*, double*, cudaStream_t);
+template cdwac_status ldlt_factor<cplx>(cdwac_ctx*, cplx*, int, cplx*, cplx*, cplx*, cudaStream_t);
+template cdwac_status ldlt_quadform<double>(cdwac_ctx*, const double*, const double*, const double*, int,
+                                            const void*, int, long, long, int, int, double*, long, double*,
+                                            cudaStream_t);
+template cdwac_status ldlt_quadform<cplx>(cdwac_ctx*, const cplx*, const cplx*, const cplx*, int, const void*, int,
+                                          long, long, int, int, cplx*, long, cplx*, cudaStream_t);

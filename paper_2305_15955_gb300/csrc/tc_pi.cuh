@@ -1,0 +1,16 @@
+// Mixed-precision polarizability on the tcgen05 tensor cores: split-BF16 operands (hi + lo, three products
+// hi*hi + hi*lo + lo*hi) with FP32 accumulation in tensor memory, written out as A = I - Pi in FP64.
+#pragma once
+#include "common.cuh"
+
+// Bytes of scratch the mixed path needs for an [n_aux][n_ov] operand (split planes, scaled planes, tables).
+size_t tc_pi_scratch_bytes(int n_aux, long n_ov);
+// Splits O^{ia} into BF16 hi/lo planes in the layout the tensor-core kernel loads (once per system).
+cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void* O_ia, int dtype, int n_aux, long n_ov, void* scratch,
+                           cudaStream_t st);
+// A = I - Pi(i xi) (real, lower triangle), xi read from xi_dev[0].
+cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const double* D, int n_aux, long n_ov, const double* xi_dev,
+                        double* A, cudaStream_t st);
+// A = I - Pi(z) (complex, lower triangle), z read from z_dev[0].
+cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const double* D, int n_aux, long n_ov, const cplx* z_dev,
+                           cplx* A, cudaStream_t st);
