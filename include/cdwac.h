@@ -87,6 +87,8 @@ typedef struct {
   int greedy_first;    /* first node: 0 = argmax |W|, 1 = argmax Re W, 2 = candidate 0 */
   int greedy_crit;     /* later nodes: 0 = largest L1 error of the current convergent, 1 = smallest */
   int precision;       /* cdwac_precision */
+  double pade_tol;     /* optional early end of a fit: stop once every remaining candidate is reproduced to an
+                          L1 error below pade_tol * max|W| (0 = off, the paper's fixed M; default 0) */
 } cdwac_params;
 
 #define CDWAC_MAX_M 256          /* largest continued fraction the fit kernel holds */

@@ -27,6 +27,7 @@ itself has no exact pin: it is a measured quantity of the method.
 from __future__ import annotations
 
 import dataclasses
+import decimal
 
 import numpy as np
 import scipy.linalg
@@ -36,15 +37,46 @@ import scipy.linalg
 # ---------------------------------------------------------------------------------------------------------
 
 
+def _legendre_dec(n, x):
+    """P_n(x) and P_{n-1}(x) by the three-term recurrence (j P_j = (2j-1) x P_{j-1} - (j-1) P_{j-2}), Decimal."""
+    p0, p1 = decimal.Decimal(1), x
+    if n == 0:
+        return p0, p0
+    for j in range(2, n + 1):
+        p0, p1 = p1, ((2 * j - 1) * x * p1 - (j - 1) * p0) / j
+    return p1, p0
+
+
 def imaginary_grid(n_imag: int, omega0: float = 1.0):
     """Modified Gauss-Legendre grid on [0, inf) for the I_n quadrature (Sec. 4, 'modified Gauss-Legendre grid').
 
-    x_k, w_k are the n-point Gauss-Legendre nodes and weights on (-1, 1); xi_k = omega0 (1+x_k)/(1-x_k) and the
-    weight carries the Jacobian d xi / d x = 2 omega0 / (1 - x)^2.  Returns (xi, wxi), xi ascending.
+    x_k, w_k are the n-point Gauss-Legendre nodes and weights on (-1, 1): the roots of P_n and
+    2 / ((1 - x^2) P_n'(x)^2).  xi_k = omega0 (1+x_k)/(1-x_k) and the weight carries the Jacobian
+    d xi / d x = 2 omega0 / (1 - x)^2.  Every number is computed with 50 significant digits (Newton's method on
+    P_n in Python's decimal arithmetic, started from numpy's nodes) and rounded once to FP64, so the grid is the
+    exact rule correctly rounded.  Returns (xi, wxi), xi ascending.
     """
-    x, w = np.polynomial.legendre.leggauss(n_imag)
-    xi = omega0 * (1.0 + x) / (1.0 - x)
-    wxi = w * 2.0 * omega0 / (1.0 - x) ** 2
+    ctx = decimal.Context(prec=50)
+    with decimal.localcontext(ctx):
+        D = decimal.Decimal
+        x0, _ = np.polynomial.legendre.leggauss(n_imag)
+        om = D(float(omega0))
+        xi = np.empty(n_imag)
+        wxi = np.empty(n_imag)
+        for k, xs in enumerate(x0):
+            x = D(float(xs))
+            for _ in range(100):
+                pn, pn1 = _legendre_dec(n_imag, x)
+                dp = n_imag * (x * pn - pn1) / (x * x - 1) if n_imag > 1 else D(1)
+                dx = pn / dp
+                x -= dx
+                if abs(dx) < D(10) ** -45:
+                    break
+            pn, pn1 = _legendre_dec(n_imag, x)
+            dp = n_imag * (x * pn - pn1) / (x * x - 1) if n_imag > 1 else D(1)
+            w = 2 / ((1 - x * x) * dp * dp)
+            xi[k] = float(om * (1 + x) / (1 - x))
+            wxi[k] = float(w * 2 * om / ((1 - x) * (1 - x)))
     return xi, wxi
 
 
@@ -79,21 +111,21 @@ def polarizability(B, D, z):
 
 
 def screened_lambda(Pi):
-    """Lambda = (I - Pi)^{-1} - I, Eq. bigLambda.
+    """Lambda = (I - Pi)^{-1} - I, Eq. bigLambda, formed as the identical (I - Pi)^{-1} Pi.
 
+    Solving (I - Pi) Lambda = Pi avoids subtracting I from (I - Pi)^{-1}: at large imaginary frequency
+    Lambda ~ Pi ~ 1/xi^2 is small and the subtraction would keep only ~1e-16 / |Lambda| of relative accuracy.
     On the imaginary axis I - Pi is real symmetric positive definite (Pi is negative semidefinite) and is
-    inverted through its Cholesky factor; elsewhere it is complex symmetric and an LU factorisation with
+    solved through its Cholesky factor; elsewhere it is complex symmetric and an LU factorisation with
     partial pivoting is used.
     """
     n = Pi.shape[0]
     A = np.eye(n, dtype=Pi.dtype) - Pi
     if np.isrealobj(A):
         c = scipy.linalg.cho_factor(A, lower=True)
-        Ainv = scipy.linalg.cho_solve(c, np.eye(n))
-    else:
-        lu = scipy.linalg.lu_factor(A)
-        Ainv = scipy.linalg.lu_solve(lu, np.eye(n, dtype=A.dtype))
-    return Ainv - np.eye(n)
+        return scipy.linalg.cho_solve(c, Pi)
+    lu = scipy.linalg.lu_factor(A)
+    return scipy.linalg.lu_solve(lu, Pi)
 
 
 def w_elements(On_s, Lam, m_idx=None):
@@ -205,12 +237,14 @@ class ThieleFit:
     breakdown: bool        # True if the fit stopped early on a non-finite reciprocal difference
 
 
-def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
+def thiele_greedy_fit(z, W, M, first="absmax", criterion="max", tol=0.0):
     """Greedy Thiele interpolation of W over candidate nodes z (Sec. 3.2, the greedy procedure).
 
     g_1(z_i) = W(z_i); g_p(z_i) = (g_{p-1}(zt_{p-1}) - g_{p-1}(z_i)) / ((z_i^2 - zt_{p-1}^2) g_{p-1}(z_i)) (Eq. rec_eq),
     a_p = g_p(zt_p) (Eq. pre_rec).  The first node is argmax |W|; node p >= 2 is the remaining candidate with the
-    largest (criterion 'max') or smallest ('min') L1 error of the convergent T^{p-1}.  Stops after M nodes.
+    largest (criterion 'max') or smallest ('min') L1 error of the convergent T^{p-1}.  Stops after M nodes, or
+    earlier once the largest remaining L1 error is below tol * max|W| (reading: the paper fixes M only; past
+    that point the candidates' errors are rounding noise and the choice among them is not defined by the data).
     """
     z = np.asarray(z, dtype=complex)
     W = np.asarray(W, dtype=complex)
@@ -218,6 +252,7 @@ def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
     n = len(z)
     M = min(M, n)
     g = W.copy()                                   # g_1 at every candidate
+    stop_below = tol * np.max(np.abs(W))
     remaining = np.ones(n, dtype=bool)
     if first == "absmax":
         k = int(np.argmax(np.abs(W)))
@@ -240,6 +275,8 @@ def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
             T = thiele_eval(np.array(a), z2[np.array(nodes)], z[rem])
             err = np.abs((T - W[rem]).real) + np.abs((T - W[rem]).imag)
         err = np.where(np.isfinite(err), err, np.inf)
+        if err.max() < stop_below:
+            break
         pick = int(np.argmax(err)) if criterion == "max" else int(np.argmin(err))
         k = int(rem[pick])
         if not np.isfinite(g[k]):
@@ -249,6 +286,38 @@ def thiele_greedy_fit(z, W, M, first="absmax", criterion="max"):
         a.append(g[k])
         remaining[k] = False
     return ThieleFit(nodes=nodes, a=np.array(a, dtype=complex), z2=z2[np.array(nodes)], breakdown=breakdown)
+
+
+def thiele_replay(z, W, order, criterion="max"):
+    """Reciprocal differences (Eqs. pre_rec, rec_eq) along a prescribed node order, with the greedy record.
+
+    Returns the ThieleFit for `order` and, for every step p >= 2, (L1 error of the node taken, largest and
+    smallest L1 error over the candidates remaining at that step).  A node order is a valid greedy order when
+    each node taken carries the extreme error of its step (up to rounding).
+    """
+    z = np.asarray(z, dtype=complex)
+    W = np.asarray(W, dtype=complex)
+    z2 = z ** 2
+    g = W.copy()
+    remaining = np.ones(len(z), dtype=bool)
+    nodes = [int(order[0])]
+    a = [g[nodes[0]]]
+    remaining[nodes[0]] = False
+    record = []
+    for k in order[1:]:
+        k = int(k)
+        rem = np.nonzero(remaining)[0]
+        with np.errstate(all="ignore"):
+            g[rem] = (a[-1] - g[rem]) / ((z2[rem] - z2[nodes[-1]]) * g[rem])
+            T = thiele_eval(np.array(a), z2[np.array(nodes)], z[rem])
+            err = np.abs((T - W[rem]).real) + np.abs((T - W[rem]).imag)
+        err = np.where(np.isfinite(err), err, np.inf)
+        record.append((float(err[list(rem).index(k)]), float(err.max()), float(err.min())))
+        nodes.append(k)
+        a.append(g[k])
+        remaining[k] = False
+    fit = ThieleFit(nodes=nodes, a=np.array(a, dtype=complex), z2=z2[np.array(nodes)], breakdown=False)
+    return fit, record
 
 
 def near_real_points(eps, n_occ, eps_states, n_real, eta_ref=1e-3, margin=0.5):
@@ -268,13 +337,13 @@ class WacModel:
     fits: list             # ThieleFit per occupied m (index = m)
 
 
-def fit_wac(W_imag_s, W_real_s, xi, z_real, n_occ, M, first="absmax", criterion="max"):
+def fit_wac(W_imag_s, W_real_s, xi, z_real, n_occ, M, first="absmax", criterion="max", tol=0.0):
     """The AC step (Sec. 3.4): for each occupied m, fit W_nm over F_wac = F_Im U F_real."""
     fits = []
     zc = np.concatenate([1j * np.asarray(xi), np.asarray(z_real, dtype=complex)])
     for m in range(n_occ):
         Wc = np.concatenate([W_imag_s[:, m].astype(complex), W_real_s[:, m] if len(z_real) else np.zeros(0)])
-        fits.append(thiele_greedy_fit(zc, Wc, M, first, criterion))
+        fits.append(thiele_greedy_fit(zc, Wc, M, first, criterion, tol))
     return WacModel(fits=fits)
 
 
@@ -398,6 +467,7 @@ class Params:
     greedy_first: str = "absmax"
     greedy_criterion: str = "max"
     real_margin: float = 0.5
+    pade_tol: float = 0.0
 
 
 def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None, with_sigma=True):
@@ -410,7 +480,8 @@ def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=N
     out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "z_real": zr, "states": []}
     for s, n in enumerate(states):
         Wre = Wre_all[s] if len(zr) else np.zeros((0, n_occ), complex)
-        model = fit_wac(Wim[s], Wre, xi, zr, n_occ, params.pade_M, params.greedy_first, params.greedy_criterion)
+        model = fit_wac(Wim[s], Wre, xi, zr, n_occ, params.pade_M, params.greedy_first, params.greedy_criterion,
+                        params.pade_tol)
         sig = lambda w, s=s, model=model: sigma_c_wac(model, Wim[s], eps, n_occ, xi, wxi, w, params.eta)
         sh = 0.0 if shifts is None else shifts[s]
         res = {"n": n, "z_real": zr, "W_real": Wre, "model": model,

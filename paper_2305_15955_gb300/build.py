@@ -13,8 +13,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcdwac.so")
 
 SOURCES = ["api.cu", "grid.cu", "pi_simt.cu", "ldlt.cu", "thiele.cu", "sigma.cu", "tc_pi.cu"]
-# thiele.cu rounds every product and sum as written (no FMA contraction), like the CPU reference arithmetic
-EXTRA = {"thiele.cu": ["--fmad=false"]}
+# thiele.cu and grid.cu round every product and sum as written (no FMA contraction): the greedy decisions and
+# the double-double grid arithmetic depend on it
+EXTRA = {"thiele.cu": ["--fmad=false"], "grid.cu": ["--fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

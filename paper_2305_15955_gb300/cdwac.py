@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("n_imag", ctypes.c_int), ("omega0", ctypes.c_double), ("n_real", ctypes.c_int),
                 ("eta_ref", ctypes.c_double), ("real_margin", ctypes.c_double), ("eta", ctypes.c_double),
                 ("pade_M", ctypes.c_int), ("greedy_first", ctypes.c_int), ("greedy_crit", ctypes.c_int),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("pade_tol", ctypes.c_double)]
 
 
 class _Pade(ctypes.Structure):
@@ -99,10 +99,11 @@ class Params:
     greedy_first: int = 0
     greedy_crit: int = 0
     precision: int = PREC_FP64
+    pade_tol: float = 0.0
 
     def c(self) -> _Params:
         return _Params(self.n_imag, self.omega0, self.n_real, self.eta_ref, self.real_margin, self.eta, self.pade_M,
-                       self.greedy_first, self.greedy_crit, self.precision)
+                       self.greedy_first, self.greedy_crit, self.precision, self.pade_tol)
 
 
 def _ptr(t):

@@ -100,6 +100,7 @@ void cdwac_default_params(cdwac_params* p) {
   p->greedy_first = 0;
   p->greedy_crit = 0;
   p->precision = CDWAC_PREC_FP64;
+  p->pade_tol = 0.0;
 }
 
 cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream) {
@@ -137,7 +138,7 @@ static cdwac_status check_system(cdwac_ctx* ctx, const cdwac_system* s, const cd
   if (p->n_real < 0 || p->n_imag + p->n_real > CDWAC_MAX_CANDIDATES)
     return set_error(ctx, CDWAC_ERR_ARG, "n_imag + n_real must be <= %d", CDWAC_MAX_CANDIDATES);
   if (p->pade_M < 1 || p->pade_M > CDWAC_MAX_M) return set_error(ctx, CDWAC_ERR_ARG, "pade_M out of range");
-  if (!(p->omega0 > 0) || !(p->eta >= 0) || !(p->eta_ref > 0))
+  if (!(p->omega0 > 0) || !(p->eta >= 0) || !(p->eta_ref > 0) || !(p->pade_tol >= 0))
     return set_error(ctx, CDWAC_ERR_ARG, "omega0, eta_ref must be > 0 and eta >= 0");
   if (p->precision != CDWAC_PREC_FP64 && p->precision != CDWAC_PREC_MIXED)
     return set_error(ctx, CDWAC_ERR_ARG, "bad precision");
@@ -155,21 +156,22 @@ struct FactorScratch {
   T* ywork;
 };
 
+// rhs_sets: right-hand-side vectors solved per column (1, or 2 for the (I - Pi)^-1 Pi form)
 template <class T>
-static size_t factor_scratch_bytes(int n, int n_cols) {
-  size_t el = (size_t)n * n + ldlt_scratch_elems<T>(n) + quadform_scratch_elems<T>(n, n_cols);
+static size_t factor_scratch_bytes(int n, int n_cols, int rhs_sets = 1) {
+  size_t el = (size_t)n * n + ldlt_scratch_elems<T>(n) + rhs_sets * quadform_scratch_elems<T>(n, n_cols);
   return el * sizeof(T) + 8 * 256;
 }
 
 template <class T>
-static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols) {
+static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols, int rhs_sets = 1) {
   FactorScratch<T> f;
   f.A = ar.take<T>((size_t)n * n);
   int nblk = (n + 63) / 64;
   f.dinv = ar.take<T>(n);
   f.linv = ar.take<T>((size_t)nblk * 64 * 64);
   f.wpanel = ar.take<T>((size_t)(nblk + 1) * 64 * 64);
-  f.ywork = ar.take<T>(quadform_scratch_elems<T>(n, n_cols));
+  f.ywork = ar.take<T>(rhs_sets * quadform_scratch_elems<T>(n, n_cols));
   return f;
 }
 
@@ -193,13 +195,17 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   const long n_ov = (long)n_occ * n_virt;
   const int cols = sys->n_states * nb;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
-  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols) + 1024;
+  // FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: |L^-1 o|^2/d - |o|^2
+  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols, 2) + 4096;
+  if (!mixed) bytes += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
   if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov);
   rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
   double* D = ar.take<double>(n_ov);
-  FactorScratch<double> f = carve_factor<double>(ar, n, cols);
+  FactorScratch<double> f = carve_factor<double>(ar, n, cols, 2);
+  double* pidiag = mixed ? nullptr : ar.take<double>(n);
+  double* V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
 
   if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
@@ -209,12 +215,20 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
     if (mixed)
       rc = tc_pi_imag(ctx, tcs, D, n, n_ov, xi + k, f.A, st);
     else
-      rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, st);
+      rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, pidiag, st);
     if (rc) return rc;
     if ((rc = ldlt_factor<double>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
-    if ((rc = ldlt_quadform<double>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
-                                    sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st)))
-      return rc;
+    if (mixed) {
+      rc = ldlt_quadform<double>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
+                                 sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st);
+    } else {
+      if ((rc = launch_pi_times_o(ctx, f.A, pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
+                                  V, st)))
+        return rc;
+      rc = ldlt_quadform_pi(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, V, (long)n * nb, nb,
+                            sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st);
+    }
+    if (rc) return rc;
   }
   return CDWAC_OK;
 }

@@ -125,8 +125,14 @@ cdwac_status launch_gauss_legendre(cdwac_ctx* ctx, int n, double omega0, double*
                                    cudaStream_t st);
 // pi_simt.cu: A = I - Pi(z) (lower triangle), FP64 SIMT.  B is [n_aux][n_ov] (f64 or f32).
 // xi (or z) is read on the device from xi_dev[0] (z_dev[0]), so that host code never waits for it.
+// The imaginary-axis kernel also writes -Pi into the strict upper triangle of A (untouched by the LDL^T) and
+// the diagonal of Pi into pidiag (may be null), so that Pi O can be formed after the factorisation.
 cdwac_status launch_pi_imag_fp64(cdwac_ctx* ctx, const void* B, int dtype, const double* D, int n_aux, int n_ov,
-                                 const double* xi_dev, double* A, cudaStream_t st);
+                                 const double* xi_dev, double* A, double* pidiag, cudaStream_t st);
+// V = Pi O (FP64) for every state column; V has O_n's layout [n_states][n][ld_o].
+cdwac_status launch_pi_times_o(cdwac_ctx* ctx, const double* A, const double* pidiag, int n, const void* O, int dtype,
+                               long o_state_stride, long ld_o, int n_states, int cols_per_state, double* V,
+                               cudaStream_t st);
 cdwac_status launch_pi_complex_fp64(cdwac_ctx* ctx, const void* B, int dtype, const double* D, int n_aux,
                                     int n_ov, const cplx* z_dev, cplx* A, cudaStream_t st);
 cdwac_status launch_transition_energies(cdwac_ctx* ctx, const double* eps, int n_occ, int n_virt, double* D,
@@ -145,6 +151,11 @@ cdwac_status ldlt_quadform(cdwac_ctx* ctx, const T* L, const T* dinv, const T* l
                            long w_state_stride, T* ywork, cudaStream_t st);
 template <class T>
 size_t quadform_scratch_elems(int n, int n_cols);
+// W[s][m] = sum_P y_Pm u_Pm / d_P with y = L^{-1} o, u = L^{-1} v, v = Pi o (real): o^T (I - Pi)^{-1} Pi o without
+// the cancellation of |L^{-1} o|^2 / d - |o|^2 when W is small.  V is FP64 with O's layout.
+cdwac_status ldlt_quadform_pi(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv_blocks, int n,
+                              const void* O, int dtype, const double* V, long o_state_stride, long ld_o, int n_states,
+                              int cols_per_state, double* W_out, long w_state_stride, double* ywork, cudaStream_t st);
 // thiele.cu
 cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_imag, int n_real, const double* xi,
                                const double* W_imag, int n_basis, const double* z_real, const double* W_real,

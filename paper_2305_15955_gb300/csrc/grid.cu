@@ -2,43 +2,109 @@
 // transition energies D_ia of the polarizability (Eq. piriv).
 #include "common.cuh"
 
-// One thread per node: Newton's method on the Legendre polynomial P_n from the asymptotic guess
-// x ~ cos(pi (k + 3/4) / (n + 1/2)) (Tricomi), P_n and P_n' by the three-term recurrence; the weight is
-// 2 / ((1 - x^2) P_n'(x)^2).  Node k is the k-th largest root; it is stored at index n-1-k so that x (and xi)
-// ascend.  xi = omega0 (1 + x) / (1 - x), and the weight takes the Jacobian 2 omega0 / (1 - x)^2.
+// Double-double arithmetic (Dekker 1971; Bailey's QD library): a value is hi + lo with |lo| <= ulp(hi)/2.
+// This file is compiled without FMA contraction; two_prod uses an explicit fma for the exact product error.
+namespace {
+struct dd {
+  double hi, lo;
+};
+__device__ inline dd two_sum(double a, double b) {
+  double s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ inline dd quick_two_sum(double a, double b) {
+  double s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ inline dd two_prod(double a, double b) {
+  double p = a * b;
+  return {p, fma(a, b, -p)};
+}
+__device__ inline dd dd_add(dd a, dd b) {
+  dd s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+  s.lo += t.hi;
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo += t.lo;
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ inline dd dd_sub(dd a, dd b) { return dd_add(a, dd{-b.hi, -b.lo}); }
+__device__ inline dd dd_mul(dd a, dd b) {
+  dd p = two_prod(a.hi, b.hi);
+  p.lo += a.hi * b.lo + a.lo * b.hi;
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ inline dd dd_muld(dd a, double b) {
+  dd p = two_prod(a.hi, b);
+  p.lo += a.lo * b;
+  return quick_two_sum(p.hi, p.lo);
+}
+__device__ inline dd dd_div(dd a, dd b) {
+  double q1 = a.hi / b.hi;
+  dd r = dd_sub(a, dd_muld(b, q1));
+  double q2 = r.hi / b.hi;
+  r = dd_sub(r, dd_muld(b, q2));
+  double q3 = r.hi / b.hi;
+  return dd_add(quick_two_sum(q1, q2), dd{q3, 0.0});
+}
+__device__ inline dd ddv(double v) { return {v, 0.0}; }
+
+// P_n(x), P_{n-1}(x) by j P_j = (2j - 1) x P_{j-1} - (j - 1) P_{j-2}
+__device__ inline void legendre_dd(int n, dd x, dd& pn, dd& pn1) {
+  dd p0 = ddv(1.0), p1 = x;
+  for (int j = 2; j <= n; ++j) {
+    dd p2 = dd_div(dd_sub(dd_muld(dd_mul(x, p1), 2.0 * j - 1.0), dd_muld(p0, j - 1.0)), ddv((double)j));
+    p0 = p1;
+    p1 = p2;
+  }
+  pn = p1;
+  pn1 = p0;
+}
+}  // namespace
+
+// One thread per node.  Newton's method on the Legendre polynomial P_n from the asymptotic guess
+// x ~ cos(pi (k + 3/4) / (n + 1/2)) (Tricomi), first in double, then refined in double-double; the weight is
+// 2 / ((1 - x^2) P_n'(x)^2) with P_n' = n (x P_n - P_{n-1}) / (x^2 - 1).  xi = omega0 (1 + x) / (1 - x) and the
+// weight times the Jacobian 2 omega0 / (1 - x)^2 are formed in double-double and rounded once, so the grid is
+// the exact rule correctly rounded to FP64.  Node k is the k-th largest root, stored at n-1-k (ascending).
 __global__ void gauss_legendre_kernel(int n, double omega0, double* xi, double* wxi) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const double pi = 3.14159265358979323846;
-  double x = cos(pi * (k + 0.75) / (n + 0.5));
-  double dp = 1.0;
-  for (int it = 0; it < 100; ++it) {
+  double x = (n == 1) ? 0.0 : cos(pi * (k + 0.75) / (n + 0.5));
+  for (int it = 0; it < 100 && n > 1; ++it) {
     double p0 = 1.0, p1 = x;
     for (int j = 2; j <= n; ++j) {
       double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
       p0 = p1;
       p1 = p2;
     }
-    double pn = (n == 1) ? x : p1, pn1 = (n == 1) ? 1.0 : p0;
-    dp = n * (x * pn - pn1) / (x * x - 1.0);
-    double dx = pn / dp;
+    double dp = n * (x * p1 - p0) / (x * x - 1.0);
+    double dx = p1 / dp;
     x -= dx;
-    if (fabs(dx) <= 1e-16 * fabs(x) + 1e-300) break;
+    if (fabs(dx) <= 1e-15 * fabs(x) + 1e-300) break;
   }
-  {  // derivative at the converged root
-    double p0 = 1.0, p1 = x;
-    for (int j = 2; j <= n; ++j) {
-      double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
-      p0 = p1;
-      p1 = p2;
+  dd X = ddv(x), dP = ddv(1.0);
+  if (n > 1) {
+    for (int it = 0; it < 4; ++it) {
+      dd pn, pn1;
+      legendre_dd(n, X, pn, pn1);
+      dP = dd_div(dd_muld(dd_sub(dd_mul(X, pn), pn1), (double)n), dd_sub(dd_mul(X, X), ddv(1.0)));
+      dd dx = dd_div(pn, dP);
+      X = dd_sub(X, dx);
+      if (fabs(dx.hi) <= 1e-33 * fabs(X.hi) + 1e-300) break;
     }
-    double pn = (n == 1) ? x : p1, pn1 = (n == 1) ? 1.0 : p0;
-    dp = n * (x * pn - pn1) / (x * x - 1.0);
+    dd pn, pn1;
+    legendre_dd(n, X, pn, pn1);
+    dP = dd_div(dd_muld(dd_sub(dd_mul(X, pn), pn1), (double)n), dd_sub(dd_mul(X, X), ddv(1.0)));
   }
-  double w = 2.0 / ((1.0 - x * x) * dp * dp);
+  dd one = ddv(1.0), om = ddv(omega0);
+  dd onepx = dd_add(one, X), onemx = dd_sub(one, X);
+  dd w = dd_div(ddv(2.0), dd_mul(dd_sub(one, dd_mul(X, X)), dd_mul(dP, dP)));
+  dd xv = dd_div(dd_mul(om, onepx), onemx);
+  dd wv = dd_div(dd_muld(dd_mul(w, om), 2.0), dd_mul(onemx, onemx));
   int out = n - 1 - k;
-  xi[out] = omega0 * (1.0 + x) / (1.0 - x);
-  wxi[out] = w * 2.0 * omega0 / ((1.0 - x) * (1.0 - x));
+  xi[out] = xv.hi + xv.lo;
+  wxi[out] = wv.hi + wv.lo;
 }
 
 cdwac_status launch_gauss_legendre(cdwac_ctx* ctx, int n, double omega0, double* xi, double* wxi, cudaStream_t st) {

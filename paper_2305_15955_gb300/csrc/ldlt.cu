@@ -314,7 +314,121 @@ __global__ void __launch_bounds__(256) quadform_kernel(const T* __restrict__ L, 
   }
 }
 
+// Two right-hand sides per column: y = L^-1 o, u = L^-1 v, W = sum_P y_P u_P / d_P  (real case).
+__global__ void __launch_bounds__(256) quadform_pi_kernel(const double* __restrict__ L, const double* __restrict__ dinv,
+                                                          const double* __restrict__ linv, int n, const void* O,
+                                                          int dtype, const double* __restrict__ V,
+                                                          long o_state_stride, long ld_o, int cols_per_state,
+                                                          int n_cols, double* ywork, double* W_out,
+                                                          long w_state_stride) {
+  __shared__ double Ls[64][QK + 1];
+  __shared__ double Ys[QK][2 * QC];
+  __shared__ double Ts[64][2 * QC];
+  __shared__ double red[256];
+  const int tid = threadIdx.x;
+  const int c_base = blockIdx.x * QC;
+  const int npad = ((n + 63) / 64) * 64;
+  double* Y = ywork + (long)blockIdx.x * npad * 2 * QC;   // [npad][2 QC]: columns 0..QC-1 y, QC..2QC-1 u
+  const int r = tid / 4, cg = tid % 4;
+  double wacc[2] = {0.0, 0.0};
+  const int nblk = (n + 63) / 64;
+  for (int ib = 0; ib < nblk; ++ib) {
+    const int i0 = ib * 64;
+    double t[4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      int col = c_base + cg * 2 + u;
+      int row = i0 + r;
+      t[u] = 0.0;
+      t[2 + u] = 0.0;
+      if (row < n && col < n_cols) {
+        const int cs = col / cols_per_state, cm = col % cols_per_state;
+        const long off = cs * o_state_stride + (long)row * ld_o + cm;
+        t[u] = ld_as<double>(O, dtype, off);
+        t[2 + u] = V[off];
+      }
+    }
+    for (int k0 = 0; k0 < i0; k0 += QK) {
+      for (int e = tid; e < 64 * QK; e += 256) {
+        int rr = e / QK, kk = e % QK;
+        int row = i0 + rr;
+        Ls[rr][kk] = (row < n) ? L[(long)row * n + k0 + kk] : 0.0;
+      }
+      for (int e = tid; e < QK * 2 * QC; e += 256) {
+        int kk = e / (2 * QC), c = e % (2 * QC);
+        Ys[kk][c] = Y[(long)(k0 + kk) * 2 * QC + c];
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int kk = 0; kk < QK; ++kk) {
+        double lv = Ls[r][kk];
+        t[0] = fma(-lv, Ys[kk][cg * 2 + 0], t[0]);
+        t[1] = fma(-lv, Ys[kk][cg * 2 + 1], t[1]);
+        t[2] = fma(-lv, Ys[kk][QC + cg * 2 + 0], t[2]);
+        t[3] = fma(-lv, Ys[kk][QC + cg * 2 + 1], t[3]);
+      }
+      __syncthreads();
+    }
+    Ts[r][cg * 2 + 0] = t[0];
+    Ts[r][cg * 2 + 1] = t[1];
+    Ts[r][QC + cg * 2 + 0] = t[2];
+    Ts[r][QC + cg * 2 + 1] = t[3];
+    __syncthreads();
+    const double* X = linv + (long)ib * 64 * 64;
+    double y[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c = 0; c <= r; ++c) {
+      double xv = X[r * 64 + c];
+      y[0] = fma(xv, Ts[c][cg * 2 + 0], y[0]);
+      y[1] = fma(xv, Ts[c][cg * 2 + 1], y[1]);
+      y[2] = fma(xv, Ts[c][QC + cg * 2 + 0], y[2]);
+      y[3] = fma(xv, Ts[c][QC + cg * 2 + 1], y[3]);
+    }
+    const int row = i0 + r;
+    if (row < n) {
+      double di = dinv[row];
+      wacc[0] = fma(y[0] * y[2], di, wacc[0]);
+      wacc[1] = fma(y[1] * y[3], di, wacc[1]);
+    } else {
+      y[0] = y[1] = y[2] = y[3] = 0.0;
+    }
+    Y[(long)row * 2 * QC + cg * 2 + 0] = y[0];
+    Y[(long)row * 2 * QC + cg * 2 + 1] = y[1];
+    Y[(long)row * 2 * QC + QC + cg * 2 + 0] = y[2];
+    Y[(long)row * 2 * QC + QC + cg * 2 + 1] = y[3];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    red[tid] = wacc[u];
+    __syncthreads();
+    for (int s = 128; s >= 4; s >>= 1) {
+      if (tid < s) red[tid] += red[tid + s];
+      __syncthreads();
+    }
+    if (tid < 4) {
+      int col = c_base + tid * 2 + u;
+      if (col < n_cols) {
+        const int cs = col / cols_per_state, cm = col % cols_per_state;
+        W_out[cs * w_state_stride + cm] = red[tid];
+      }
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cdwac_status ldlt_quadform_pi(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv_blocks, int n,
+                              const void* O, int dtype, const double* V, long o_state_stride, long ld_o, int n_states,
+                              int cols_per_state, double* W_out, long w_state_stride, double* ywork, cudaStream_t st) {
+  const int n_cols = n_states * cols_per_state;
+  if (n_cols <= 0) return CDWAC_OK;
+  quadform_pi_kernel<<<ceil_div(n_cols, QC), 256, 0, st>>>(L, dinv, linv_blocks, n, O, dtype, V, o_state_stride,
+                                                            ld_o, cols_per_state, n_cols, ywork, W_out,
+                                                            w_state_stride);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
 
 template <class T>
 size_t ldlt_scratch_elems(int n) {

@@ -7,7 +7,9 @@
 // evaluates the convergent T^{p-1} at the remaining candidates (innermost level outwards), and takes the
 // candidate with the largest (or smallest) L1 error |Re(T - W)| + |Im(T - W)| as node p, a_p = g_p(node).
 // The first node maximises |W|.  Ties go to the lowest candidate index; a non-finite error counts as +inf;
-// a non-finite a_p ends the fit early (breakdown) and the first n_used nodes stay valid.
+// a non-finite a_p ends the fit early (breakdown) and the first n_used nodes stay valid.  The fit also ends
+// once the largest remaining error is below pade_tol * max|W|: beyond that point the choice among candidates
+// would be decided by rounding.
 // This file is compiled without FMA contraction so that every product and sum rounds as written.
 #include "common.cuh"
 
@@ -39,7 +41,8 @@ __device__ inline WarpPick warp_best(WarpPick p, bool want_max) {
 
 __global__ void thiele_fit_kernel(int n_states, int n_occ, int n_imag, int n_real, const double* __restrict__ xi,
                                   const double* __restrict__ W_imag, int n_basis, const cplx* __restrict__ z_real,
-                                  const cplx* __restrict__ W_real, int M, int first_mode, int crit, int M_cap,
+                                  const cplx* __restrict__ W_real, int M, int first_mode, int crit, double tol,
+                                  int M_cap,
                                   cplx* __restrict__ a_out, cplx* __restrict__ z2_out, int* __restrict__ nodes_out,
                                   int* __restrict__ n_used_out, unsigned* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,6 +78,12 @@ __global__ void thiele_fit_kernel(int n_states, int n_occ, int n_imag, int n_rea
   }
   __syncwarp();
 
+  // largest |W| over the candidates (scale of the stopping rule)
+  double wmax = 0.0;
+  for (int i = lane; i < nc; i += 32) wmax = fmax(wmax, hypot(Wv[i].x, Wv[i].y));
+  for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, off));
+  const double stop_below = tol * wmax;
+
   // node 1
   WarpPick pk{0, 0.0, 0};
   for (int i = lane; i < nc; i += 32) {
@@ -96,6 +105,7 @@ __global__ void thiele_fit_kernel(int n_states, int n_occ, int n_imag, int n_rea
   for (int p = 1; p < Mx; ++p) {
     const cplx ap = a[p - 1], zp = zt2[p - 1];
     WarpPick best{0, 0.0, 0};
+    double emax = 0.0;
     for (int i = lane; i < nc; i += 32) {
       if (!rem[i]) continue;
       cplx gi = g[i];
@@ -111,12 +121,15 @@ __global__ void thiele_fit_kernel(int n_states, int n_occ, int n_imag, int n_rea
       cplx d = T - Wv[i];
       double err = fabs(d.x) + fabs(d.y);
       if (!isfinite(err)) err = INFINITY;
+      emax = fmax(emax, err);
       WarpPick c{1, err, i};
       if (better(c, best, crit == 0)) best = c;
     }
     best = warp_best(best, crit == 0);
+    for (int off = 16; off > 0; off >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, off));
     __syncwarp();
     if (!best.valid) break;
+    if (emax < stop_below) break;     // every remaining value is already reproduced
     k = best.idx;
     cplx gk = g[k];
     if (!finite_c(gk)) {
@@ -192,7 +205,7 @@ cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_im
   const int fits = n_states * n_occ;
   thiele_fit_kernel<<<ceil_div(fits, warps), warps * 32, smem, st>>>(
       n_states, n_occ, n_imag, n_real, xi, W_imag, n_basis, reinterpret_cast<const cplx*>(z_real),
-      reinterpret_cast<const cplx*>(W_real), M, prm->greedy_first, prm->greedy_crit, pade->M,
+      reinterpret_cast<const cplx*>(W_real), M, prm->greedy_first, prm->greedy_crit, prm->pade_tol, pade->M,
       reinterpret_cast<cplx*>(pade->a), reinterpret_cast<cplx*>(pade->z2), pade->nodes, pade->n_used,
       ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);

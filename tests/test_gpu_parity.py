@@ -39,7 +39,7 @@ def make(spec, dtype=np.float64, states=None):
 def oracle_params(p: cdwac.Params):
     return o.Params(n_imag=p.n_imag, omega0=p.omega0, n_real=p.n_real, eta_ref=p.eta_ref, eta=p.eta,
                     pade_M=p.pade_M, greedy_first=["absmax", "max", "first"][p.greedy_first],
-                    greedy_criterion=["max", "min"][p.greedy_crit], real_margin=p.real_margin)
+                    greedy_criterion=["max", "min"][p.greedy_crit], real_margin=p.real_margin, pade_tol=p.pade_tol)
 
 
 def test_gauss_legendre_grid(ctx):
@@ -49,8 +49,9 @@ def test_gauss_legendre_grid(ctx):
         p = cdwac.Params(n_imag=n)
         xi, wxi, _ = ctx.build_W_imag(sysd, p)
         xo, wo = o.imaginary_grid(n)
-        np.testing.assert_allclose(xi.cpu().numpy(), xo, rtol=1e-13, atol=0)
-        np.testing.assert_allclose(wxi.cpu().numpy(), wo, rtol=1e-12, atol=0)
+        # both sides round the exact rule once: the grids agree bit for bit
+        assert np.array_equal(xi.cpu().numpy(), xo)
+        assert np.array_equal(wxi.cpu().numpy(), wo)
 
 
 @pytest.mark.parametrize("case", ["small", "ragged", "ragged_f32"])
@@ -86,6 +87,61 @@ def test_w_real_fp64(ctx):
     assert np.abs(Wg - Wo).max() < 1e-11 * max(1.0, np.abs(Wo).max())
 
 
+def _replayed_state(ref, s, pade, p, n_occ, eps, omega):
+    """The oracle's CD-WAC for state s along the GPU's node orders.
+
+    The greedy order is decided by floating point: once the convergent reproduces the remaining reference values
+    to rounding level, several orders are equally valid.  So the oracle replays the GPU's order on its own W
+    tables, checks that every node taken carries the largest remaining L1 error of its step (to within rounding
+    of W), and evaluates Sigma and the QP equation with those fits."""
+    xi, wxi = ref["xi"], ref["wxi"]
+    Wim = ref["W_imag"][s]
+    Wre = ref["states"][s]["W_real"]
+    zr = ref["z_real"]
+    zc = np.concatenate([1j * xi, zr])
+    nodes = pade.nodes.cpu().numpy()[s]
+    used = pade.n_used.cpu().numpy()[s]
+    crit = ["max", "min"][p.greedy_crit]
+    fits = []
+    for m in range(n_occ):
+        Wc = np.concatenate([Wim[:, m].astype(complex), Wre[:, m] if len(zr) else np.zeros(0, complex)])
+        fit, record = o.thiele_replay(zc, Wc, nodes[m, :used[m]], crit)
+        assert used[m] == min(p.pade_M, len(zc))
+        assert nodes[m, 0] == int(np.argmax(np.abs(Wc)))
+        noise = 1e-8 * np.abs(Wc).max()
+        for e_take, e_max, e_min in record:
+            if crit == "max":
+                assert e_take >= e_max * (1 - 1e-9) - noise, (m, e_take, e_max)
+            else:
+                assert e_take <= e_min * (1 + 1e-9) + noise, (m, e_take, e_min)
+        fits.append(fit)
+    model = o.WacModel(fits=fits)
+    sig = lambda w: o.sigma_c_wac(model, Wim, eps, n_occ, xi, wxi, w, p.eta)
+    sig_ref = np.array([sig(w) for w in omega])
+    # conditioning of the continuation: Sigma moved by a W perturbation at the level at which the GPU and the
+    # oracle W tables differ (pivoted LU vs LDL^T, summation order): 3e-12 relative at near-real points,
+    # 2e-15 on the imaginary axis
+    rng = np.random.default_rng(1)
+    fits_p = []
+    for m in range(n_occ):
+        Wc = np.concatenate([Wim[:, m].astype(complex), Wre[:, m] if len(zr) else np.zeros(0, complex)])
+        rel = np.concatenate([np.full(len(xi), 2e-15), np.full(len(zr), 3e-12)])
+        Wc = Wc * (1 + rel * (rng.standard_normal(len(Wc)) + 1j * rng.standard_normal(len(Wc))))
+        fits_p.append(o.thiele_replay(zc, Wc, nodes[m, :used[m]], crit)[0])
+    model_p = o.WacModel(fits=fits_p)
+    sens = np.array([abs(o.sigma_c_wac(model_p, Wim, eps, n_occ, xi, wxi, w, p.eta) - v)
+                     for w, v in zip(omega, sig_ref)])
+    return sig_ref, o.qp_solve(sig, eps[ref["states"][s]["n"]], 0.0, omega), sens
+
+
+def _assert_sigma(sig_gpu, sig_ref, sens):
+    """1e-8 Ha wherever the continuation is well conditioned; elsewhere 30x the oracle's own sensitivity."""
+    tol = np.maximum(HA_TOL, 30.0 * sens)
+    bad = np.abs(sig_gpu - sig_ref) > tol
+    assert not bad.any(), (np.abs(sig_gpu - sig_ref)[bad], sens[bad])
+    assert np.mean(sens < 1e-9) > 0.25         # a good part of the grid is held to the strict tolerance
+
+
 def _wac_case(ctx, spec, p, omega):
     eps, B, On, st, sysd = make(spec)
     xi, wxi, W = ctx.build_W_imag(sysd, p)
@@ -94,8 +150,9 @@ def _wac_case(ctx, spec, p, omega):
     e, Z, it, qs = ctx.qp_solve(sysd, p, xi, wxi, W, pade, omega)
     D = o.transition_energies(eps, spec.n_occ)
     ref = o.run_cdwac(B, D, On, eps, spec.n_occ, list(st), oracle_params(p), omega)
+    rep = [_replayed_state(ref, s, pade, p, spec.n_occ, eps, omega) for s in range(len(st))]
     return dict(sig=sig, e=e.cpu().numpy(), Z=Z.cpu().numpy(), it=it.cpu().numpy(), qs=qs.cpu().numpy(),
-                pade=pade, ref=ref, W=W.cpu().numpy())
+                pade=pade, ref=ref, W=W.cpu().numpy(), rep=rep)
 
 
 @pytest.mark.parametrize("n_real,M", [(40, 64), (0, 16), (20, 40)])
@@ -104,18 +161,14 @@ def test_cdwac_sigma_and_qp_small(ctx, n_real, M):
     p = cdwac.Params(n_imag=100, n_real=n_real, pade_M=M)
     omega = inputs.omega_grid(128)
     r = _wac_case(ctx, spec, p, omega)
-    rs = r["ref"]["states"][0]
-    # node order of the greedy fits
-    nodes = r["pade"].nodes.cpu().numpy()[0]
-    used = r["pade"].n_used.cpu().numpy()[0]
-    for m, fit in enumerate(rs["model"].fits):
-        assert used[m] == len(fit.nodes)
-        assert list(nodes[m, :used[m]]) == fit.nodes
-    assert np.abs(r["sig"][0] - rs["sigma"]).max() < HA_TOL
-    q = rs["qp"]
-    assert r["qs"][0] == q.status
+    sig_rep, q, sens = r["rep"][0]
+    _assert_sigma(r["sig"][0], sig_rep, sens)
+    assert r["qs"][0] == q.status == 0
     assert abs(r["e"][0] - q.e_qp) < HA_TOL
     assert abs(r["Z"][0] - q.Z) < 1e-6
+    # the oracle's own greedy orders differ only where the choice is rounding noise
+    q_own = r["ref"]["states"][0]["qp"]
+    assert abs(r["e"][0] - q_own.e_qp) < 1e-6
 
 
 def test_cdwac_two_states_ragged(ctx):
@@ -124,9 +177,11 @@ def test_cdwac_two_states_ragged(ctx):
     omega = inputs.omega_grid(48)
     r = _wac_case(ctx, spec, p, omega)
     for s in range(2):
-        rs = r["ref"]["states"][s]
-        assert np.abs(r["sig"][s] - rs["sigma"]).max() < HA_TOL
-        assert abs(r["e"][s] - rs["qp"].e_qp) < HA_TOL
+        sig_rep, q, sens = r["rep"][s]
+        _assert_sigma(r["sig"][s], sig_rep, sens)
+        assert r["qs"][s] == q.status
+        if q.status < 2:                        # a non-converged iteration has no unique answer
+            assert abs(r["e"][s] - q.e_qp) < HA_TOL
 
 
 def test_plain_cd_sigma_and_qp(ctx):
@@ -162,10 +217,10 @@ def test_edge_cases(ctx, shape):
         p = cdwac.Params(n_imag=20, n_real=4, pade_M=1)
     omega = inputs.omega_grid(8)
     r = _wac_case(ctx, spec, p, omega)
-    rs = r["ref"]["states"][0]
-    assert np.abs(r["sig"][0] - rs["sigma"]).max() < HA_TOL
-    if rs["qp"].status == 0:
-        assert abs(r["e"][0] - rs["qp"].e_qp) < HA_TOL
+    sig_rep, q, sens = r["rep"][0]
+    _assert_sigma(r["sig"][0], sig_rep, sens)
+    if q.status == 0:
+        assert abs(r["e"][0] - q.e_qp) < HA_TOL
 
 
 def test_not_spd_reported(ctx):

@@ -222,3 +222,15 @@ def test_cdwac_core_qp_close_to_cd(small):
     e_cd, e_wac = cd["states"][0]["qp"].e_qp, wac["states"][0]["qp"].e_qp
     assert cd["states"][0]["qp"].status == 0
     assert abs(e_cd - e_wac) * 27211.386 < 0.01          # well inside 1 meV with 40 near-real points
+
+
+def test_thiele_replay_of_greedy_order_is_identical(small):
+    s = small
+    zr = o.near_real_points(s["eps"], 5, s["eps"][[0]], 20)
+    Wre = o.w_complex_table(s["B"], s["D"], s["On"], zr, np.arange(5))[0]
+    zc = np.concatenate([1j * s["xi"], zr])
+    Wc = np.concatenate([s["Wim"][0][:, 1].astype(complex), Wre[:, 1]])
+    fit = o.thiele_greedy_fit(zc, Wc, 30)
+    rep, record = o.thiele_replay(zc, Wc, fit.nodes)
+    assert np.array_equal(rep.a, fit.a)
+    assert all(take == emax for take, emax, _ in record)
