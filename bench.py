@@ -1,0 +1,398 @@
+"""Benchmark of the CD-WAC core-level G0W0 hot path on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole path for one synthetic system: W_nm(i xi) on the 100-point imaginary grid
+(Pi on the tensor cores, FP64 LDL^T, W projection), 40 near-real reference points (complex Pi, complex LDL^T),
+greedy Thiele fits for every occupied m, Sigma_c on a 128-point real-frequency grid and the QP equation.
+The headline value is core-state Sigma_c(omega) evaluations per second over whole steps; the line also carries
+the QP solve time (= ms_per_step), Sigma evals/s with the W tables already built, the plain-CD cost on the same
+GPU, the accuracy against the FP64 oracle, the roofline of the dominant kernel and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload acene|small]
+  torchrun --nproc-per-node N bench.py --gpus N ...   (N > 1: independent replicas, one system per rank)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "core-state Sigma_c(w) evals/sec and QP solve time, CD-WAC vs plain CD on 1 GB300 at <=1 meV"
+UNIT = "Sigma_c evals/s"
+HA_PER_MEV = 1.0 / 27211.386
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["acene", "small"], default="acene")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain-CD and CPU-baseline measurements")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_2305_15955_gb300 import inputs
+    if name == "acene":
+        spec = inputs.acene_system(1)
+        desc = ("acene-like: N_basis=1200 (6 core at -10.6+-0.01 Ha, 114 valence in [-1.2,-0.25], 1080 virtual "
+                "log-spaced in [0.01,5]), N_aux=4000, seed 1, core state n=0; 100 imaginary GL points, 40 near-real "
+                "points, greedy Thiele M=64, 128 omega in [-11,-10] Ha")
+    else:
+        spec = inputs.small_system()
+        desc = "small: N_basis=40, N_aux=120, seed 0, core state n=0; 100 GL points, 40 near-real, M=64, 128 omega"
+    return spec, desc
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    return dist.get_rank(), ws, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value, device):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands, on a bounded sample of the same workload
+# ------------------------------------------------------------------------------------------------------------
+
+def oracle_sample(spec, B, On, eps):
+    """Time the oracle on one imaginary frequency (Pi, Cholesky solve, W for every m) and scale to a whole step:
+    100 imaginary points + 40 near-real points (complex arithmetic, counted as 4x an imaginary point).
+    Returns (seconds per step, seconds measured)."""
+    from oracle import cdwac_oracle as o
+    D = o.transition_energies(eps, spec.n_occ)
+    xi, _ = o.imaginary_grid(100)
+    t0 = time.perf_counter()
+    Lam = o.screened_lambda(o.polarizability(B, D, 1j * xi[50]))
+    o.w_elements(On[0], Lam)
+    t_imag = time.perf_counter() - t0
+    return t_imag * (100 + 4 * 40), t_imag
+
+
+def run_reference(args, rank, ws, dist):
+    if rank != 0:
+        return
+    from paper_2305_15955_gb300 import inputs
+    spec, desc = workload(args.workload)
+    eps = inputs.eigenvalues(spec)
+    B = inputs.build_B(spec)
+    On = inputs.build_On(spec)
+    for _ in range(args.warmup):
+        oracle_sample(spec, B, On, eps)
+    est, meas = [], 0.0
+    for _ in range(args.steps):
+        s, m = oracle_sample(spec, B, On, eps)
+        est.append(s)
+        meas += m
+    t_step = float(np.mean(est))
+    value = len(spec.states) * 128 / t_step
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "W_nm(i xi) at 1 of 100 imaginary frequencies per step (numpy/OpenBLAS FP64), "
+                                       "scaled by 100 + 4*40 points; fits and Sigma not counted (negligible)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------------------
+
+def run_ours(args, rank, ws, dist):
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2305_15955_gb300 import cdwac, inputs
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        g.build()
+    barrier(dist)
+    g.build()
+    spec, desc = workload(args.workload)
+    mixed = args.precision == "mixed"
+    odt = np.float32 if mixed else np.float64
+    eps = inputs.eigenvalues(spec)
+    B = inputs.build_B(spec, dtype=odt)
+    On = inputs.build_On(spec, dtype=odt)
+    omega = inputs.omega_grid(128)
+    sysd = cdwac.System(eps, B, On, spec.states, spec.n_occ, device=dev)
+    prm = cdwac.Params(n_imag=100, n_real=40, pade_M=64,
+                       precision=cdwac.PREC_MIXED if mixed else cdwac.PREC_FP64)
+    ctx = cdwac.Context(local)
+    omega_d = torch.as_tensor(omega, device=dev)
+    pade = ctx.alloc_pade(sysd, prm)
+
+    def step(system):
+        xi, wxi, W = ctx.build_W_imag(system, prm, sync=False)
+        ctx.fit_pade(system, prm, xi, W, pade, sync=False)
+        sig = ctx.sigma(system, prm, xi, wxi, W, pade, omega_d, sync=False)
+        e, Z, it, qs = ctx.qp_solve(system, prm, xi, wxi, W, pade, omega_d, sync=False)
+        return xi, wxi, W, sig, e, Z, it, qs
+
+    allow = (cdwac.ERR_PADE_BREAKDOWN, cdwac.ERR_QP_NOT_CONVERGED)   # recorded in the line, not fatal
+    for _ in range(args.warmup):
+        out = step(sysd)
+    ctx.sync_status(allow)
+    torch.cuda.synchronize()
+    barrier(dist)
+
+    stream = torch.cuda.current_stream()
+    ctx.profile(True)
+    ctx.profile_read()
+    launches0 = ctx.launch_count()
+    with ClockSampler(local) as clk:
+        barrier(dist)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step(sysd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(dist)
+    ctx.sync_status(allow)
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(dist, ms, dev)
+    n_eval = len(spec.states) * len(omega)
+    value = ws * n_eval / (ms / 1e3)
+    xi, wxi, W, sig, e, Z, it, qs = out
+    e_qp = float(e.cpu()[0])
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16x3-f32acc+f64" if mixed else "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": args.precision,
+                       "l2": "inputs larger than L2 (O^ia = %.2f GB)" % (B.nbytes / 1e9),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "qp_solve_ms": ms, "qp": {"e_qp_Ha": e_qp, "Z": float(Z.cpu()[0]), "iterations": int(it.cpu()[0]),
+                                      "status": int(qs.cpu()[0])},
+            "gpu_launches": int(launches // args.steps)}
+
+    # per-kernel breakdown and roofline of the dominant kernel
+    peaks, peak_kind = measured_peaks()
+    tot = sum(v[1] for v in prof.values()) or 1.0
+    line["kernels"] = {k: {"regions": v[0] // args.steps, "ms_per_step": v[1] / args.steps,
+                           "share": v[1] / tot} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    n, nov = spec.n_aux, spec.n_ov
+    pi_flops = n * (n + 1) / 2 * nov * 2.0               # lower triangle, 1 MAC = 2 flops
+    rl = {}
+    if "pi_tc_imag" in prof:
+        cnt, tms = prof["pi_tc_imag"]
+        ach = pi_flops / (tms / cnt / 1e3) / 1e12
+        pk = peaks["bf16_tflops_sustained"] / 3.0
+        rl["pi_tc_imag"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                            "traffic": None,
+                            "peak_basis": f"bf16_tflops_sustained/3 ({peak_kind}): three BF16 products per MAC",
+                            "algorithmic_flops_per_launch": pi_flops}
+    if "ldlt_fp64" in prof:
+        cnt, tms = prof["ldlt_fp64"]
+        n_real_f = prm.n_real
+        flops = (prm.n_imag * n ** 3 / 3.0 + n_real_f * 4.0 * n ** 3 / 3.0) / (prm.n_imag + n_real_f)
+        ach = flops / (tms / cnt / 1e3) / 1e12
+        rl["ldlt_fp64"] = {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                           "traffic": None, "peak_basis": "nominal FP64 1.25 TFLOP/s (FMA pipe; 1.20 measured)",
+                           "algorithmic_flops_per_launch": flops}
+    if dom in rl:
+        line["roofline"] = rl[dom]
+        line["roofline"]["kernel"] = dom
+    elif rl:
+        k0 = next(iter(rl))
+        line["roofline"] = dict(rl[k0], kernel=k0)
+    line["roofline_all"] = rl
+    line["clocks"] = clk.summary()
+
+    if rank == 0 and not args.no_extras:
+        # Sigma throughput with the W tables and fits already built (the CD-WAC residue term is a fraction)
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        many = torch.linspace(-11.0, -10.0, 4096, dtype=torch.float64, device=dev)
+        ctx.sigma(sysd, prm, xi, wxi, W, pade, many, sync=False)
+        t0.record(stream)
+        for _ in range(5):
+            ctx.sigma(sysd, prm, xi, wxi, W, pade, many, sync=False)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        line["sigma_evals_per_s_after_setup"] = 5 * 4096 / (t0.elapsed_time(t1) / 1e3)
+
+        # plain CD on the same GPU: one Sigma evaluation builds Pi(z) and a complex LDL^T per residue
+        w1 = torch.tensor([e_qp], dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        ctx.sigma(sysd, prm, xi, wxi, W, None, w1, sync=True)
+        t_cd = time.perf_counter() - tp
+        n_res = int(np.sum(eps[:spec.n_occ] > e_qp))
+        line["plain_cd"] = {"sigma_eval_s": t_cd, "residues_per_eval": n_res, "per_residue_ms": 1e3 * t_cd / max(1, n_res),
+                            "sigma_evals_per_s": 1.0 / t_cd,
+                            "qp_solve_s_extrapolated": t_cd * (int(it.cpu()[0]) + 2),
+                            "note": "one plain-CD Sigma(omega) timed at omega = e_qp; the QP time is that cost times "
+                                    "the CD-WAC iteration count + 2 (Z), extrapolated"}
+        line["cdwac_vs_plain_cd_qp_speedup_extrapolated"] = line["plain_cd"]["qp_solve_s_extrapolated"] / (ms / 1e3)
+
+        # accuracy against the FP64 oracle (stored by tests/golden/make_acene_reference.py)
+        gold = os.path.join(ROOT, "tests", "golden", "acene_1200_cdwac_oracle.json")
+        if args.workload == "acene" and os.path.exists(gold):
+            with open(gold) as f:
+                ref = json.load(f)
+            line["accuracy"] = {"qp_vs_fp64_oracle_meV": (e_qp - ref["qp"]["e_qp"]) / HA_PER_MEV,
+                                "oracle": "tests/golden/acene_1200_cdwac_oracle.json"}
+
+        # end to end through the C ABI with host buffers: copies of the inputs in, QP energy and Sigma out
+        Bh = torch.from_numpy(B).pin_memory()
+        Onh = torch.from_numpy(On).pin_memory()
+        epsh = torch.from_numpy(eps).pin_memory()
+        Bd, Ond, epsd = torch.empty_like(Bh, device=dev), torch.empty_like(Onh, device=dev), torch.empty_like(epsh, device=dev)
+        sys_e2e = cdwac.System(epsd, Bd, Ond, spec.states, spec.n_occ, device=dev)
+        e_host = torch.empty(len(spec.states), dtype=torch.float64).pin_memory()
+        s_host = torch.empty(len(spec.states), len(omega), dtype=torch.complex128).pin_memory()
+
+        def e2e_step():
+            Bd.copy_(Bh, non_blocking=True)
+            Ond.copy_(Onh, non_blocking=True)
+            epsd.copy_(epsh, non_blocking=True)
+            o = step(sys_e2e)
+            e_host.copy_(o[4], non_blocking=True)
+            s_host.copy_(o[3], non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+        ms_e2e = t0.elapsed_time(t1) / args.steps
+        line["e2e"] = {"value": n_eval / (ms_e2e / 1e3), "unit": UNIT,
+                       "h2d_bytes_per_step": int(Bh.numel() * Bh.element_size() + Onh.numel() * Onh.element_size()
+                                                 + epsh.numel() * 8),
+                       "d2h_bytes_per_step": int(e_host.numel() * 8 + s_host.numel() * 16), "ms_per_step": ms_e2e}
+
+        # CPU oracle on this host's cores (bounded sample)
+        B64 = B.astype(np.float64)
+        On64 = On.astype(np.float64)
+        t_step, t_meas = oracle_sample(spec, B64, On64, eps)
+        line["cpu_baseline"] = {"value": n_eval / t_step, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"W_nm(i xi) at 1 of 100 imaginary frequencies ({t_meas:.1f} s, numpy FP64), "
+                                          "scaled by 100 + 4*40 points per step"}
+    ctx.sync_status(allow)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    rank, ws, dist = dist_init()
+    if args.impl == "reference":
+        run_reference(args, rank, ws, dist)
+    else:
+        run_ours(args, rank, ws, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -120,6 +120,25 @@ cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream);
 /* Bytes of context scratch currently held (grows on demand, released by cdwac_destroy). */
 size_t cdwac_scratch_bytes(const cdwac_ctx* ctx);
 
+/* ---- tracing ------------------------------------------------------------------------------------------ */
+
+/* One kernel class of the event profiler: name (static string), launches of the class and their summed device
+ * time (CUDA events recorded on the call's stream around each launch or launch group). */
+typedef struct {
+  const char* name;
+  int launches;
+  double total_ms;
+} cdwac_profile_entry;
+
+/* Turns the per-kernel-class CUDA-event timers on or off (off by default; on adds two event records per timed
+ * region and no synchronisation). */
+void cdwac_profile_enable(cdwac_ctx* ctx, int on);
+/* Waits for the recorded events, writes up to max_entries classes into out (classes never timed are skipped),
+ * clears the accumulated times and returns the number written (negative on a CUDA error). */
+int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries);
+/* Kernels launched through this context since it was created. */
+long long cdwac_launch_count(const cdwac_ctx* ctx);
+
 /* ---- the four steps ----------------------------------------------------------------------------------- */
 
 /* W_nm(i xi_k) on the imaginary grid: the wmatrix(F_Im) step (Sec. 3.4; Eqs. piriv, bigLambda, wriv).

@@ -25,7 +25,8 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
-            "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve"]
+            "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
+            "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count"]
 
 
 class CdwacError(RuntimeError):
@@ -45,6 +46,10 @@ class _Params(ctypes.Structure):
                 ("eta_ref", ctypes.c_double), ("real_margin", ctypes.c_double), ("eta", ctypes.c_double),
                 ("pade_M", ctypes.c_int), ("greedy_first", ctypes.c_int), ("greedy_crit", ctypes.c_int),
                 ("precision", ctypes.c_int), ("pade_tol", ctypes.c_double)]
+
+
+class _ProfEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("launches", ctypes.c_int), ("total_ms", ctypes.c_double)]
 
 
 class _Pade(ctypes.Structure):
@@ -82,6 +87,11 @@ def load():
     lib.cdwac_sigma.argtypes = [P, sysp, prmp, P, P, P, padep, P, ctypes.c_int, P, P]
     lib.cdwac_qp_solve.argtypes = [P, sysp, prmp, P, P, P, padep, P, P, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_int, P, P, P, P, P]
+    lib.cdwac_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.cdwac_profile_enable.restype = None
+    lib.cdwac_profile_read.argtypes = [P, ctypes.POINTER(_ProfEntry), ctypes.c_int]
+    lib.cdwac_launch_count.argtypes = [P]
+    lib.cdwac_launch_count.restype = ctypes.c_longlong
     _lib = lib
     return lib
 
@@ -196,6 +206,21 @@ class Context:
 
     def scratch_bytes(self) -> int:
         return int(self.lib.cdwac_scratch_bytes(self.h))
+
+    def profile(self, on: bool = True):
+        """Per-kernel-class CUDA-event timers (recorded on the calls' stream)."""
+        self.lib.cdwac_profile_enable(self.h, 1 if on else 0)
+
+    def profile_read(self) -> dict:
+        """{class: (launch groups timed, total ms)} accumulated since the last read (waits for the events)."""
+        buf = (_ProfEntry * 32)()
+        k = self.lib.cdwac_profile_read(self.h, buf, 32)
+        if k < 0:
+            raise CdwacError(ERR_CUDA, "cdwac_profile_read failed")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(k)}
+
+    def launch_count(self) -> int:
+        return int(self.lib.cdwac_launch_count(self.h))
 
     def _dev(self):
         return torch.device("cuda", self.device)

@@ -75,9 +75,50 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
   return CDWAC_OK;
 }
 
+static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",  "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
+                                              "ldlt_fp64", "w_solves", "thiele_fit", "sigma",         "qp_solve"};
+
+void cdwac_profile_enable(cdwac_ctx* ctx, int on) {
+  if (ctx) ctx->prof = on != 0;
+}
+
+int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries) {
+  if (!ctx) return -1;
+  for (auto& r : ctx->prof_live) {
+    if (cudaEventSynchronize(r.stop) != cudaSuccess) return -1;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.start, r.stop) != cudaSuccess) return -1;
+    ctx->prof_ms[r.cls] += ms;
+    ctx->prof_n[r.cls] += 1;
+    ctx->prof_pool.push_back(r.start);
+    ctx->prof_pool.push_back(r.stop);
+  }
+  ctx->prof_live.clear();
+  int k = 0;
+  for (int c = 0; c < PROF_COUNT && k < max_entries; ++c) {
+    if (ctx->prof_n[c] == 0) continue;
+    out[k].name = kProfNames[c];
+    out[k].launches = ctx->prof_n[c];
+    out[k].total_ms = ctx->prof_ms[c];
+    ++k;
+  }
+  for (int c = 0; c < PROF_COUNT; ++c) {
+    ctx->prof_ms[c] = 0;
+    ctx->prof_n[c] = 0;
+  }
+  return k;
+}
+
+long long cdwac_launch_count(const cdwac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
 void cdwac_destroy(cdwac_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  for (auto& r : ctx->prof_live) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -175,13 +216,6 @@ static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols, int rhs_sets 
   return f;
 }
 
-// Mixed-precision operand planes of B = O^{ia}, built once per system and cached by pointer identity.
-struct MixedCache {
-  const void* src = nullptr;
-  int n_aux = 0;
-  long n_ov = 0;
-};
-
 extern "C" {
 
 cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
@@ -208,16 +242,28 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   double* V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
 
-  if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
-  if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
-  if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+  {
+    ProfScope ps(ctx, PROF_GRID, st);
+    if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
+    if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
+  }
+  if (mixed) {
+    ProfScope ps(ctx, PROF_PI_PREP, st);
+    if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+  }
   for (int k = 0; k < prm->n_imag; ++k) {
-    if (mixed)
-      rc = tc_pi_imag(ctx, tcs, D, n, n_ov, xi + k, f.A, st);
-    else
+    if (mixed) {
+      rc = tc_pi_imag(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, xi + k, f.A, st);
+    } else {
+      ProfScope ps(ctx, PROF_PI_SIMT, st);
       rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, pidiag, st);
+    }
     if (rc) return rc;
-    if ((rc = ldlt_factor<double>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+    {
+      ProfScope ps(ctx, PROF_LDLT, st);
+      if ((rc = ldlt_factor<double>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+    }
+    ProfScope ps(ctx, PROF_QUADFORM, st);
     if (mixed) {
       rc = ldlt_quadform<double>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
                                  sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st);
@@ -265,19 +311,29 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
     if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, nr, prm->eta_ref, prm->real_margin,
                                       reinterpret_cast<double*>(zr), st)))
       return rc;
-    if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+    if (mixed) {
+      ProfScope ps(ctx, PROF_PI_PREP, st);
+      if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+    }
     for (int j = 0; j < nr; ++j) {
-      if (mixed)
-        rc = tc_pi_complex(ctx, tcs, D, n, n_ov, zr + j, f.A, st);
-      else
+      if (mixed) {
+        rc = tc_pi_complex(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, zr + j, f.A, st);
+      } else {
+        ProfScope ps(ctx, PROF_PI_SIMT, st);
         rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zr + j, f.A, st);
+      }
       if (rc) return rc;
-      if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      {
+        ProfScope ps(ctx, PROF_LDLT, st);
+        if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      }
+      ProfScope ps(ctx, PROF_QUADFORM, st);
       if ((rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns,
                                     n_occ, Wr + (long)j * n_occ, (long)nr * n_occ, f.ywork, st)))
         return rc;
     }
   }
+  ProfScope ps(ctx, PROF_THIELE, st);
   return launch_thiele_fit(ctx, ns, n_occ, prm->n_imag, nr, xi, W_imag, nb, reinterpret_cast<const double*>(zr),
                            reinterpret_cast<const double*>(Wr), prm, pade, st);
 }
@@ -325,7 +381,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
       set_z_kernel<<<1, 1, 0, st>>>(zdev, fabs(eps[m] - w), prm->eta);
       CDWAC_LAUNCH_CHECK(ctx);
       if (mixed)
-        rc = tc_pi_complex(ctx, tcs, D, n, n_ov, zdev, f.A, st);
+        rc = tc_pi_complex(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, zdev, f.A, st);
       else
         rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zdev, f.A, st);
       if (rc) return rc;
@@ -357,7 +413,10 @@ cdwac_status cdwac_sigma(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_pa
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   if (n_omega == 0) return CDWAC_OK;
-  if ((rc = launch_sigma_wac(ctx, sys, prm, xi, wxi, W_imag, pade, omega, n_omega, sigma, st))) return rc;
+  {
+    ProfScope ps(ctx, PROF_SIGMA, st);
+    if ((rc = launch_sigma_wac(ctx, sys, prm, xi, wxi, W_imag, pade, omega, n_omega, sigma, st))) return rc;
+  }
   if (pade) return CDWAC_OK;
   // plain CD: residues need the frequencies and eigenvalues on the host
   std::vector<double> w(n_omega), e(sys->n_basis);
@@ -472,9 +531,11 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
     return set_error(ctx, CDWAC_ERR_ARG, "pade arrays do not match the system");
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  if (pade)
+  if (pade) {
+    ProfScope ps(ctx, PROF_QP, st);
     return launch_qp_wac(ctx, sys, prm, xi, wxi, W_imag, pade, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters,
                          qp_status, st);
+  }
   // plain CD: host-driven iteration per state
   const int ns = sys->n_states, nb = sys->n_basis;
   std::vector<double> e(nb), grid(n_grid), sh(ns, 0.0);

@@ -6,6 +6,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/cdwac.h"
 
@@ -19,6 +20,26 @@ enum : unsigned {
   DEV_ERR_BOUNDS = 1u << 5,
 };
 
+// Kernel classes timed by the optional event profiler (cdwac_profile_enable).
+enum ProfClass {
+  PROF_GRID = 0,
+  PROF_PI_PREP,       // BF16 split / weighted split of the operand planes
+  PROF_PI_TC_IMAG,    // tcgen05 Pi(i xi)
+  PROF_PI_TC_CPLX,    // tcgen05 Pi(z)
+  PROF_PI_SIMT,       // FP64 Pi on the CUDA cores
+  PROF_LDLT,          // blocked LDL^T (FP64, real or complex)
+  PROF_QUADFORM,      // Pi O product and triangular solves for W
+  PROF_THIELE,
+  PROF_SIGMA,
+  PROF_QP,
+  PROF_COUNT
+};
+
+struct ProfRecord {
+  int cls;
+  cudaEvent_t start, stop;
+};
+
 struct cdwac_ctx {
   int device = 0;
   int num_sms = 0;
@@ -27,6 +48,40 @@ struct cdwac_ctx {
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   std::string last_error;
+  long long launches = 0;           // kernels launched through this context
+  bool prof = false;
+  std::vector<ProfRecord> prof_live;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[PROF_COUNT] = {};
+  int prof_n[PROF_COUNT] = {};
+};
+
+// Records CUDA events around a region on `st` when profiling is on.
+struct ProfScope {
+  cdwac_ctx* ctx;
+  cudaStream_t st;
+  int cls;
+  cudaEvent_t stop = nullptr;
+  ProfScope(cdwac_ctx* c, int k, cudaStream_t s) : ctx(c), st(s), cls(k) {
+    if (!ctx->prof) return;
+    cudaEvent_t a = take(), b = take();
+    cudaEventRecord(a, st);
+    ctx->prof_live.push_back({cls, a, b});
+    stop = b;
+  }
+  ~ProfScope() {
+    if (stop) cudaEventRecord(stop, st);
+  }
+  cudaEvent_t take() {
+    if (!ctx->prof_pool.empty()) {
+      cudaEvent_t e = ctx->prof_pool.back();
+      ctx->prof_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
 };
 
 // Bump allocator over the context scratch; every region is 256-byte aligned.
@@ -54,7 +109,11 @@ cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...);
                        cudaGetErrorString(e_));                                                   \
   } while (0)
 
-#define CDWAC_LAUNCH_CHECK(ctx) CDWAC_CUDA_TRY(ctx, cudaGetLastError())
+#define CDWAC_LAUNCH_CHECK(ctx)            \
+  do {                                     \
+    ++(ctx)->launches;                     \
+    CDWAC_CUDA_TRY(ctx, cudaGetLastError()); \
+  } while (0)
 
 // ---- complex scalar (re, im) with the operations the kernels need ------------------------------------------
 struct cplx {

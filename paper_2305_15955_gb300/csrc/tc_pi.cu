@@ -1,13 +1,510 @@
-// Placeholder until the tcgen05 kernel lands: the mixed path reports UNSUPPORTED.
+// Mixed-precision polarizability on the 5th-generation tensor cores (tcgen05), GB300 / sm_103a.
+//
+//   A = I - Pi(z),  Pi(z) = B diag(w(z)) B^T,  w = 2 [1/(z - D) - 1/(z + D)] = 4 D / (z^2 - D^2)   (Eq. piriv)
+//
+// The weight is folded into one operand: S = B diag(-w) (per column ia), so that A = I + S B^T.  Each of S and B is
+// split into BF16 planes hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the product is formed from three BF16
+// products hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (the lo*lo term, ~2^-16 relative, is
+// dropped).  On the imaginary axis -w = 4 D / (xi^2 + D^2) > 0 and one real accumulator is used; for complex z
+// the real and imaginary parts of -w give two scaled operands that share the loaded B tile (two accumulators).
+//
+// Kernel: one CTA per 128 x 128 tile of the lower triangle of A (lower-triangle tiles only: A is symmetric),
+// 128 threads.  Warp 0 lane 0 drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory
+// stages; warp 1 owns the tensor memory and lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction,
+// both operands K-major); tcgen05.commit releases a stage when the MMAs reading it finish.  All four warps then
+// read the accumulator rows they own (tcgen05.ld 32x32b) and write A in FP64.  Every wait on an mbarrier is
+// bounded (5 s): on expiry the kernel records CDWAC_ERR_TIMEOUT, stops issuing, drains what it issued and frees
+// its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <string.h>
+
 #include "tc_pi.cuh"
 
-size_t tc_pi_scratch_bytes(int, long) { return 256; }
-cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void*, int, int, long, void*, cudaStream_t) {
-  return set_error(ctx, CDWAC_ERR_UNSUPPORTED, "mixed precision not built");
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int PLANE = BM * BK * 2;                       // bytes of one 128 x 64 BF16 operand tile
+constexpr unsigned long long WAIT_NS = 5000000000ull;     // bound of every mbarrier wait
+
+struct Maps {
+  CUtensorMap a0h, a0l, a1h, a1l, bh, bl;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
 }
-cdwac_status tc_pi_imag(cdwac_ctx* ctx, void*, const double*, int, long, const double*, double*, cudaStream_t) {
-  return set_error(ctx, CDWAC_ERR_UNSUPPORTED, "mixed precision not built");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
-cdwac_status tc_pi_complex(cdwac_ctx* ctx, void*, const double*, int, long, const cplx*, cplx*, cudaStream_t) {
-  return set_error(ctx, CDWAC_ERR_UNSUPPORTED, "mixed precision not built");
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 0) {
+      if (abort_flag && *abort_flag) return false;
+      if (gtime() - t0 > WAIT_NS) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major operand in the 128-byte swizzle layout written by TMA: rows of 128 B,
+// 8-row groups 1024 B apart (stride byte offset), leading byte offset unused for this layout, version 1.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+// Instruction descriptor of tcgen05.mma.kind::f16: FP32 accumulator, BF16 A and B, both K-major, N, M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
+  int t = int((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+  while ((t + 1) * (t + 2) / 2 <= b) ++t;
+  while (t * (t + 1) / 2 > b) --t;
+  ti = t;
+  tj = b - t * (t + 1) / 2;
+}
+
+template <int NACC>
+struct Cfg {
+  static constexpr int NPL = 2 * NACC + 2;                 // operand planes per stage
+  static constexpr int STAGE = NPL * PLANE;
+  static constexpr int STAGES = NACC == 1 ? 3 : 2;
+  static constexpr int SMEM = STAGES * STAGE + 1024;       // + alignment slack
+  static constexpr int TMEM_COLS = NACC == 1 ? 128 : 256;
+};
+
+// A = I + S B^T (lower triangle).  NACC == 1: real A (double*).  NACC == 2: complex A (cplx*), re from S0, im from S1.
+template <int NACC>
+__global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
+                                                         void* A_out, unsigned* status) {
+  using C = Cfg<NACC>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, consumed;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int ti, tj;
+  lower_tile_coords(blockIdx.x, ti, tj);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % C::STAGES;
+      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], (uint32_t)C::STAGE);
+      uint8_t* st = smem + s * C::STAGE;
+      const int x = kt * BK;
+      tma_load_2d(&maps.a0h, &full_bar[s], st + 0 * PLANE, x, ti * BM);
+      tma_load_2d(&maps.a0l, &full_bar[s], st + 1 * PLANE, x, ti * BM);
+      if (NACC == 2) {
+        tma_load_2d(&maps.a1h, &full_bar[s], st + 2 * PLANE, x, ti * BM);
+        tma_load_2d(&maps.a1l, &full_bar[s], st + 3 * PLANE, x, ti * BM);
+      }
+      tma_load_2d(&maps.bh, &full_bar[s], st + (2 * NACC) * PLANE, x, tj * BN);
+      tma_load_2d(&maps.bl, &full_bar[s], st + (2 * NACC + 1) * PLANE, x, tj * BN);
+    }
+    issued = kt;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % C::STAGES;
+      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * C::STAGE);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
+        const uint64_t bh = sdesc(base + (2 * NACC) * PLANE + ko), bl = sdesc(base + (2 * NACC + 1) * PLANE + ko);
+        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) {
+          const uint64_t ah = sdesc(base + (2 * a) * PLANE + ko), al = sdesc(base + (2 * a + 1) * PLANE + ko);
+          const uint32_t d = tmem + a * BN;
+          umma(d, ah, bh, idesc, acc);
+          umma(d, ah, bl, idesc, 1u);
+          umma(d, al, bh, idesc, 1u);
+        }
+      }
+      umma_commit(&empty_bar[s]);
+    }
+    consumed = kt;
+    umma_commit(&done_bar);   // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // ---- epilogue: warp w reads accumulator lanes 32w..32w+31 = rows of the tile
+  const bool done_ok = mbar_wait(&done_bar, 0, nullptr);
+  tc_fence_after();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!done_ok || abort_flag) {
+      raise_status(status, DEV_ERR_TIMEOUT);
+      // drain loads that were issued but never consumed, so no copy lands after the CTA exits
+      for (int kt = consumed; kt < issued; ++kt)
+        mbar_wait(&full_bar[kt % C::STAGES], (uint32_t)(kt / C::STAGES) & 1u, nullptr);
+    }
+  }
+  if (done_ok && !abort_flag) {
+    const int row = ti * BM + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v0[32], v1[32];
+      tmem_ld32(tmem + lane_base + c0, v0);
+      if (NACC == 2) tmem_ld32(tmem + lane_base + BN + c0, v1);
+      const int col0 = tj * BN + c0;
+      if (row < n) {
+        if (NACC == 1) {
+          double* Ar = reinterpret_cast<double*>(A_out) + (long)row * n;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            if (col <= row && col < n) Ar[col] = (col == row ? 1.0 : 0.0) + (double)__uint_as_float(v0[j]);
+          }
+        } else {
+          cplx* Ac = reinterpret_cast<cplx*>(A_out) + (long)row * n;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            if (col <= row && col < n)
+              Ac[col] = mkc((col == row ? 1.0 : 0.0) + (double)__uint_as_float(v0[j]), (double)__uint_as_float(v1[j]));
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ---- operand preparation (HBM-bound elementwise passes) ---------------------------------------------------------
+
+__device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
+  __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    h[j] = __float2bfloat16_rn(v[j]);
+    l[j] = __float2bfloat16_rn(v[j] - __bfloat162float(h[j]));
+  }
+  hi = *reinterpret_cast<uint4*>(h);
+  lo = *reinterpret_cast<uint4*>(l);
+}
+
+template <class TIn>
+__device__ __forceinline__ void load8(const TIn* row, long k, long n_ov, float (&v)[8]) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = (k + j < n_ov) ? (float)row[k + j] : 0.f;
+}
+
+// B -> hi/lo planes [n][kpad] (zero padded along K)
+template <class TIn>
+__global__ void split_kernel(const TIn* __restrict__ B, int n, long n_ov, long kpad, __nv_bfloat16* __restrict__ hi,
+                             __nv_bfloat16* __restrict__ lo) {
+  const long chunks = kpad / 8, total = (long)n * chunks;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < total; c += (long)gridDim.x * blockDim.x) {
+    const long r = c / chunks, k = (c % chunks) * 8;
+    float v[8];
+    load8(B + r * n_ov, k, n_ov, v);
+    uint4 h, l;
+    split8(v, h, l);
+    *reinterpret_cast<uint4*>(hi + r * kpad + k) = h;
+    *reinterpret_cast<uint4*>(lo + r * kpad + k) = l;
+  }
+}
+
+// per-column weights: imaginary axis  w0 = 4 D / (xi^2 + D^2);  complex  (w0, w1) = -4 D / (z^2 - D^2)
+__global__ void weight_kernel(const double* __restrict__ D, long n_ov, long kpad, const double* xi_dev,
+                              const cplx* z_dev, float* __restrict__ w0, float* __restrict__ w1) {
+  for (long k = blockIdx.x * (long)blockDim.x + threadIdx.x; k < kpad; k += (long)gridDim.x * blockDim.x) {
+    if (k >= n_ov) {
+      w0[k] = 0.f;
+      if (w1) w1[k] = 0.f;
+      continue;
+    }
+    const double d = D[k];
+    if (xi_dev) {
+      const double x = xi_dev[0];
+      w0[k] = (float)(4.0 * d / (x * x + d * d));
+    } else {
+      const cplx z = z_dev[0];
+      const cplx w = mkc(-4.0 * d, 0.0) / (z * z - mkc(d * d, 0.0));
+      w0[k] = (float)w.x;
+      w1[k] = (float)w.y;
+    }
+  }
+}
+
+// S_a = B diag(w_a) -> hi/lo planes, for one (NACC = 1) or two (NACC = 2) weight vectors
+template <class TIn, int NACC>
+__global__ void scale_split_kernel(const TIn* __restrict__ B, int n, long n_ov, long kpad, const float* __restrict__ w0,
+                                   const float* __restrict__ w1, __nv_bfloat16* __restrict__ s0h,
+                                   __nv_bfloat16* __restrict__ s0l, __nv_bfloat16* __restrict__ s1h,
+                                   __nv_bfloat16* __restrict__ s1l) {
+  const long chunks = kpad / 8, total = (long)n * chunks;
+  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < total; c += (long)gridDim.x * blockDim.x) {
+    const long r = c / chunks, k = (c % chunks) * 8;
+    float v[8], s[8];
+    load8(B + r * n_ov, k, n_ov, v);
+    const float4 wa = *reinterpret_cast<const float4*>(w0 + k), wb = *reinterpret_cast<const float4*>(w0 + k + 4);
+    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] = v[j] * wv[j];
+    uint4 h, l;
+    split8(s, h, l);
+    *reinterpret_cast<uint4*>(s0h + r * kpad + k) = h;
+    *reinterpret_cast<uint4*>(s0l + r * kpad + k) = l;
+    if (NACC == 2) {
+      const float4 xa = *reinterpret_cast<const float4*>(w1 + k), xb = *reinterpret_cast<const float4*>(w1 + k + 4);
+      const float xv[8] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) s[j] = v[j] * xv[j];
+      split8(s, h, l);
+      *reinterpret_cast<uint4*>(s1h + r * kpad + k) = h;
+      *reinterpret_cast<uint4*>(s1l + r * kpad + k) = l;
+    }
+  }
+}
+
+// ---- host side --------------------------------------------------------------------------------------------------
+
+struct Scratch {
+  __nv_bfloat16 *bh, *bl, *s0h, *s0l, *s1h, *s1l;
+  float *w0, *w1;
+  long kpad;
+};
+
+long kpad_of(long n_ov) { return ((n_ov + BK - 1) / BK) * BK; }
+
+Scratch carve(void* base, int n, long n_ov) {
+  Scratch s;
+  const long kp = kpad_of(n_ov);
+  const size_t plane = (size_t)n * kp;
+  Arena ar(base);
+  s.bh = ar.take<__nv_bfloat16>(plane);
+  s.bl = ar.take<__nv_bfloat16>(plane);
+  s.s0h = ar.take<__nv_bfloat16>(plane);
+  s.s0l = ar.take<__nv_bfloat16>(plane);
+  s.s1h = ar.take<__nv_bfloat16>(plane);
+  s.s1l = ar.take<__nv_bfloat16>(plane);
+  s.w0 = ar.take<float>(kp);
+  s.w1 = ar.take<float>(kp);
+  s.kpad = kp;
+  return s;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, long kpad) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int elementwise_blocks(cdwac_ctx* ctx, long work) {
+  long b = (work + 255) / 256;
+  long cap = (long)ctx->num_sms * 8;
+  return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
+}
+
+template <int NACC>
+cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, cudaStream_t st) {
+  using C = Cfg<NACC>;
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  bool ok = make_map(&maps.a0h, s.s0h, n, s.kpad) && make_map(&maps.a0l, s.s0l, n, s.kpad) &&
+            make_map(&maps.bh, s.bh, n, s.kpad) && make_map(&maps.bl, s.bl, n, s.kpad);
+  if (NACC == 2) ok = ok && make_map(&maps.a1h, s.s1h, n, s.kpad) && make_map(&maps.a1l, s.s1l, n, s.kpad);
+  if (!ok) return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel<NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  const int nt = (n + BM - 1) / BM;
+  tc_syrk_kernel<NACC><<<nt * (nt + 1) / 2, 128, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+}  // namespace
+
+size_t tc_pi_scratch_bytes(int n_aux, long n_ov) {
+  const long kp = kpad_of(n_ov);
+  return 256 + 6 * ((size_t)n_aux * kp * 2 + 256) + 2 * ((size_t)kp * 4 + 256) + 1024;
+}
+
+cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void* O_ia, int dtype, int n_aux, long n_ov, void* scratch,
+                           cudaStream_t st) {
+  Scratch s = carve(scratch, n_aux, n_ov);
+  const int blocks = elementwise_blocks(ctx, (long)n_aux * (s.kpad / 8));
+  if (dtype == CDWAC_F64)
+    split_kernel<double><<<blocks, 256, 0, st>>>((const double*)O_ia, n_aux, n_ov, s.kpad, s.bh, s.bl);
+  else
+    split_kernel<float><<<blocks, 256, 0, st>>>((const float*)O_ia, n_aux, n_ov, s.kpad, s.bh, s.bl);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+static cdwac_status scale(cdwac_ctx* ctx, const Scratch& s, const void* O_ia, int dtype, const double* D, int n,
+                          long n_ov, const double* xi_dev, const cplx* z_dev, cudaStream_t st) {
+  const int wb = elementwise_blocks(ctx, s.kpad);
+  weight_kernel<<<wb, 256, 0, st>>>(D, n_ov, s.kpad, xi_dev, z_dev, s.w0, z_dev ? s.w1 : nullptr);
+  CDWAC_LAUNCH_CHECK(ctx);
+  const int blocks = elementwise_blocks(ctx, (long)n * (s.kpad / 8));
+  if (xi_dev) {
+    if (dtype == CDWAC_F64)
+      scale_split_kernel<double, 1><<<blocks, 256, 0, st>>>((const double*)O_ia, n, n_ov, s.kpad, s.w0, nullptr, s.s0h,
+                                                           s.s0l, nullptr, nullptr);
+    else
+      scale_split_kernel<float, 1><<<blocks, 256, 0, st>>>((const float*)O_ia, n, n_ov, s.kpad, s.w0, nullptr, s.s0h,
+                                                          s.s0l, nullptr, nullptr);
+  } else {
+    if (dtype == CDWAC_F64)
+      scale_split_kernel<double, 2><<<blocks, 256, 0, st>>>((const double*)O_ia, n, n_ov, s.kpad, s.w0, s.w1, s.s0h,
+                                                           s.s0l, s.s1h, s.s1l);
+    else
+      scale_split_kernel<float, 2><<<blocks, 256, 0, st>>>((const float*)O_ia, n, n_ov, s.kpad, s.w0, s.w1, s.s0h,
+                                                          s.s0l, s.s1h, s.s1l);
+  }
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
+                        long n_ov, const double* xi_dev, double* A, cudaStream_t st) {
+  Scratch s = carve(scratch, n_aux, n_ov);
+  cdwac_status rc;
+  {
+    ProfScope ps(ctx, PROF_PI_PREP, st);
+    rc = scale(ctx, s, O_ia, dtype, D, n_aux, n_ov, xi_dev, nullptr, st);
+  }
+  if (rc) return rc;
+  ProfScope ps(ctx, PROF_PI_TC_IMAG, st);
+  return run_syrk<1>(ctx, s, n_aux, A, st);
+}
+
+cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
+                           long n_ov, const cplx* z_dev, cplx* A, cudaStream_t st) {
+  Scratch s = carve(scratch, n_aux, n_ov);
+  cdwac_status rc;
+  {
+    ProfScope ps(ctx, PROF_PI_PREP, st);
+    rc = scale(ctx, s, O_ia, dtype, D, n_aux, n_ov, nullptr, z_dev, st);
+  }
+  if (rc) return rc;
+  ProfScope ps(ctx, PROF_PI_TC_CPLX, st);
+  return run_syrk<2>(ctx, s, n_aux, A, st);
 }

@@ -3,14 +3,15 @@
 #pragma once
 #include "common.cuh"
 
-// Bytes of scratch the mixed path needs for an [n_aux][n_ov] operand (split planes, scaled planes, tables).
+// Bytes of scratch the mixed path needs for an [n_aux][n_ov] operand (split planes, scaled planes, weights).
 size_t tc_pi_scratch_bytes(int n_aux, long n_ov);
 // Splits O^{ia} into BF16 hi/lo planes in the layout the tensor-core kernel loads (once per system).
 cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void* O_ia, int dtype, int n_aux, long n_ov, void* scratch,
                            cudaStream_t st);
-// A = I - Pi(i xi) (real, lower triangle), xi read from xi_dev[0].
-cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const double* D, int n_aux, long n_ov, const double* xi_dev,
-                        double* A, cudaStream_t st);
+// A = I - Pi(i xi) (real, lower triangle), xi read from xi_dev[0].  O_ia is the source of the planes built by
+// tc_pi_prepare (its weighted copy is re-split for every frequency).
+cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
+                        long n_ov, const double* xi_dev, double* A, cudaStream_t st);
 // A = I - Pi(z) (complex, lower triangle), z read from z_dev[0].
-cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const double* D, int n_aux, long n_ov, const cplx* z_dev,
-                           cplx* A, cudaStream_t st);
+cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
+                           long n_ov, const cplx* z_dev, cplx* A, cudaStream_t st);
