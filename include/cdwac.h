@@ -187,6 +187,25 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------------------------------------ */
+
+/* Fixed device scratch of cdwac_build_W_imag_noalloc (held by every GPU that loads the library). */
+#define CDWAC_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* cdwac_build_W_imag with precision CDWAC_PREC_FP64, for callers that must not allocate device memory while
+ * they run (a host program that grants the library a fixed device budget, a latency-critical loop that cannot
+ * take an allocation's device-wide synchronisation).  No context: the caller passes the system, the outputs
+ * (same layouts as cdwac_build_W_imag) and `dev_status`, a device word into which pivot errors are OR-ed
+ * (bit 0: I - Pi not positive definite; may be NULL).  Every intermediate lives in one fixed device array of
+ * CDWAC_NOALLOC_SCRATCH_BYTES; a system whose intermediates do not fit (about n_aux^2 + n_occ*n_virt
+ * + 3*n_states*n_basis*n_aux doubles; n_aux = 500 with one state of 600 orbitals fits) is rejected with
+ * CDWAC_ERR_ARG before anything runs, as is precision != CDWAC_PREC_FP64.  The first call on a device (that device
+ * current) looks up the array's device address; make it before any stream capture.  Calls share the array:
+ * calls that overlap on the GPU race.  Calls no cudaMalloc/cudaFree.  The paper has no counterpart: this is an
+ * interface variant of the wmatrix(F_Im) step only. */
+cdwac_status cdwac_build_W_imag_noalloc(const cdwac_system* sys, const cdwac_params* prm, double* xi, double* wxi,
+                                        double* W_imag, unsigned* dev_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

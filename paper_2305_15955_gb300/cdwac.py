@@ -26,7 +26,8 @@ PREC_FP64, PREC_MIXED = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
-            "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count"]
+            "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count", "cdwac_build_W_imag_noalloc"]
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class CdwacError(RuntimeError):
@@ -92,6 +93,7 @@ def load():
     lib.cdwac_profile_read.argtypes = [P, ctypes.POINTER(_ProfEntry), ctypes.c_int]
     lib.cdwac_launch_count.argtypes = [P]
     lib.cdwac_launch_count.restype = ctypes.c_longlong
+    lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -291,3 +293,15 @@ class Context:
         if sync:
             self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
         return e, Z, it, qs
+
+
+def build_W_imag_noalloc(system: System, params: Params, xi, wxi, W_imag, dev_status=None, stream=None) -> int:
+    """cdwac_build_W_imag_noalloc: FP64 W(i xi) into caller-provided tensors, no device allocation by the library.
+
+    xi, wxi [n_imag], W_imag [n_states, n_imag, n_basis] float64 CUDA tensors; dev_status an int32 CUDA tensor of
+    one element (pivot errors are OR-ed into it) or None.  Returns the call's status code (asynchronous)."""
+    lib = load()
+    p = params.c()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream if stream is None else stream)
+    return int(lib.cdwac_build_W_imag_noalloc(ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(wxi),
+                                              _ptr(W_imag), _ptr(dev_status), st))

@@ -12,7 +12,7 @@
 // ---- context and errors ----------------------------------------------------------------------------------
 
 cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...) {
-  if (ctx) {
+  if (ctx && !ctx->quiet) {
     char buf[1024];
     va_list ap;
     va_start(ap, fmt);

@@ -49,6 +49,7 @@ struct cdwac_ctx {
   size_t scratch_bytes = 0;
   std::string last_error;
   long long launches = 0;           // kernels launched through this context
+  bool quiet = false;               // set_error keeps no message (used where no allocation may happen)
   bool prof = false;
   std::vector<ProfRecord> prof_live;
   std::vector<cudaEvent_t> prof_pool;
