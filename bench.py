@@ -37,9 +37,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["acene", "small"], default="acene")
+    ap.add_argument("--workload", choices=["acene", "medium", "small"], default="acene")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain-CD and CPU-baseline measurements")
+    ap.add_argument("--n-imag", type=int, default=100, help="imaginary grid points (100 = the workload's value)")
+    ap.add_argument("--n-real", type=int, default=40, help="near-real reference points (40 = the workload's value)")
     return ap.parse_args()
 
 
@@ -50,6 +52,10 @@ def workload(name):
         desc = ("acene-like: N_basis=1200 (6 core at -10.6+-0.01 Ha, 114 valence in [-1.2,-0.25], 1080 virtual "
                 "log-spaced in [0.01,5]), N_aux=4000, seed 1, core state n=0; 100 imaginary GL points, 40 near-real "
                 "points, greedy Thiele M=64, 128 omega in [-11,-10] Ha")
+    elif name == "medium":
+        spec = inputs.custom_system(600, 60, 2000, seed=1, n_core=6, states=(0,))
+        desc = ("medium acene-like: N_basis=600 (6 core, 54 valence, 540 virtual), N_aux=2000, seed 1, core state "
+                "n=0; O^ia = 0.26 GB FP32 (above L2); 100 GL points, 40 near-real, M=64, 128 omega")
     else:
         spec = inputs.small_system()
         desc = "small: N_basis=40, N_aux=120, seed 0, core state n=0; 100 GL points, 40 near-real, M=64, 128 omega"
@@ -215,7 +221,7 @@ def run_ours(args, rank, ws, dist):
     On = inputs.build_On(spec, dtype=odt)
     omega = inputs.omega_grid(128)
     sysd = cdwac.System(eps, B, On, spec.states, spec.n_occ, device=dev)
-    prm = cdwac.Params(n_imag=100, n_real=40, pade_M=64,
+    prm = cdwac.Params(n_imag=args.n_imag, n_real=args.n_real, pade_M=min(64, args.n_imag + args.n_real),
                        precision=cdwac.PREC_MIXED if mixed else cdwac.PREC_FP64)
     ctx = cdwac.Context(local)
     omega_d = torch.as_tensor(omega, device=dev)
@@ -263,7 +269,8 @@ def run_ours(args, rank, ws, dist):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16x3-f32acc+f64" if mixed else "f64", "data": "synthetic",
-            "config": {"workload": desc, "precision": args.precision,
+            "config": {"workload": desc if (args.n_imag, args.n_real) == (100, 40) else
+                       desc + f" [reduced: n_imag={args.n_imag}, n_real={args.n_real}]", "precision": args.precision,
                        "l2": "inputs larger than L2 (O^ia = %.2f GB)" % (B.nbytes / 1e9),
                        "parallelism": "replicas" if ws > 1 else "single GPU"},
             "qp_solve_ms": ms, "qp": {"e_qp_Ha": e_qp, "Z": float(Z.cpu()[0]), "iterations": int(it.cpu()[0]),

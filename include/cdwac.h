@@ -130,8 +130,8 @@ typedef struct {
   double total_ms;
 } cdwac_profile_entry;
 
-/* Turns the per-kernel-class CUDA-event timers on or off (off by default; on adds two event records per timed
- * region and no synchronisation). */
+/* Per-kernel-class CUDA-event timers: on = 0 off (default), 1 kernel classes, 2 also each launch of the LDL^T
+ * block steps (diag / panel / update).  Adds two event records per timed region and no synchronisation. */
 void cdwac_profile_enable(cdwac_ctx* ctx, int on);
 /* Waits for the recorded events, writes up to max_entries classes into out (classes never timed are skipped),
  * clears the accumulated times and returns the number written (negative on a CUDA error). */

@@ -209,9 +209,9 @@ class Context:
     def scratch_bytes(self) -> int:
         return int(self.lib.cdwac_scratch_bytes(self.h))
 
-    def profile(self, on: bool = True):
-        """Per-kernel-class CUDA-event timers (recorded on the calls' stream)."""
-        self.lib.cdwac_profile_enable(self.h, 1 if on else 0)
+    def profile(self, on=True):
+        """Per-kernel-class CUDA-event timers (recorded on the calls' stream); on=2 also times the LDL^T steps."""
+        self.lib.cdwac_profile_enable(self.h, int(on))
 
     def profile_read(self) -> dict:
         """{class: (launch groups timed, total ms)} accumulated since the last read (waits for the events)."""

@@ -64,6 +64,12 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
     return CDWAC_ERR_UNSUPPORTED;
   }
   ctx->num_sms = p.multiProcessorCount;
+  if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_bulk, cudaEventDisableTiming) != cudaSuccess) {
+    delete ctx;
+    return CDWAC_ERR_CUDA;
+  }
   if (cudaMalloc(&ctx->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess) {
@@ -75,11 +81,12 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
   return CDWAC_OK;
 }
 
-static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",  "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
-                                              "ldlt_fp64", "w_solves", "thiele_fit", "sigma",         "qp_solve"};
+static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",   "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
+                                              "ldlt_fp64", "w_solves",  "thiele_fit", "sigma",         "qp_solve",
+                                              "ldlt_diag", "ldlt_panel", "ldlt_update"};
 
 void cdwac_profile_enable(cdwac_ctx* ctx, int on) {
-  if (ctx) ctx->prof = on != 0;
+  if (ctx) ctx->prof = on < 0 ? 0 : (on > 2 ? 2 : on);
 }
 
 int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries) {
@@ -119,6 +126,9 @@ void cdwac_destroy(cdwac_ctx* ctx) {
     cudaEventDestroy(r.stop);
   }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+  if (ctx->ev_panel) cudaEventDestroy(ctx->ev_panel);
+  if (ctx->ev_bulk) cudaEventDestroy(ctx->ev_bulk);
+  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (ctx->d_status) cudaFree(ctx->d_status);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -211,7 +221,7 @@ static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols, int rhs_sets 
   int nblk = (n + 63) / 64;
   f.dinv = ar.take<T>(n);
   f.linv = ar.take<T>((size_t)nblk * 64 * 64);
-  f.wpanel = ar.take<T>((size_t)(nblk + 1) * 64 * 64);
+  f.wpanel = ar.take<T>(2 * (size_t)(nblk + 1) * 64 * 64);
   f.ywork = ar.take<T>(rhs_sets * quadform_scratch_elems<T>(n, n_cols));
   return f;
 }
@@ -230,17 +240,19 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   const int cols = sys->n_states * nb;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
   // FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: |L^-1 o|^2/d - |o|^2
-  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols, 2) + 4096;
+  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols, mixed ? 0 : 2) + 4096;
   if (!mixed) bytes += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
-  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov);
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) + 512;
   rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
   double* D = ar.take<double>(n_ov);
-  FactorScratch<double> f = carve_factor<double>(ar, n, cols, 2);
+  FactorScratch<double> f = carve_factor<double>(ar, n, cols, mixed ? 0 : 2);
   double* pidiag = mixed ? nullptr : ar.take<double>(n);
   double* V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+  float* negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
+  void* ws32 = mixed ? ar.take<char>(wsolve32_scratch_bytes(n, cols)) : nullptr;
 
   {
     ProfScope ps(ctx, PROF_GRID, st);
@@ -253,7 +265,7 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   }
   for (int k = 0; k < prm->n_imag; ++k) {
     if (mixed) {
-      rc = tc_pi_imag(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, xi + k, f.A, st);
+      rc = tc_pi_imag(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, xi + k, f.A, negpi32, st);
     } else {
       ProfScope ps(ctx, PROF_PI_SIMT, st);
       rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, pidiag, st);
@@ -265,8 +277,8 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
     }
     ProfScope ps(ctx, PROF_QUADFORM, st);
     if (mixed) {
-      rc = ldlt_quadform<double>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
-                                 sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st);
+      rc = wsolve32(ctx, f.A, f.dinv, f.linv, negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
+                    W_imag + (long)k * nb, (long)prm->n_imag * nb, ws32, st);
     } else {
       if ((rc = launch_pi_times_o(ctx, f.A, pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
                                   V, st)))
@@ -297,7 +309,7 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
   size_t bytes = n_ov * sizeof(double) + 2 * sizeof(cplx) * (size_t)ns * nr * (n_occ + 1) + 4096;
   if (nr > 0) bytes += factor_scratch_bytes<cplx>(n, ns * n_occ);
-  if (mixed && nr > 0) bytes += tc_pi_scratch_bytes(n, n_ov);
+  if (mixed && nr > 0) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ);
   rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
@@ -307,6 +319,7 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
   if (nr > 0) {
     FactorScratch<cplx> f = carve_factor<cplx>(ar, n, ns * n_occ);
     void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+    void* wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns * n_occ)) : nullptr;
     if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
     if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, nr, prm->eta_ref, prm->real_margin,
                                       reinterpret_cast<double*>(zr), st)))
@@ -328,9 +341,13 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
         if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
       }
       ProfScope ps(ctx, PROF_QUADFORM, st);
-      if ((rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns,
-                                    n_occ, Wr + (long)j * n_occ, (long)nr * n_occ, f.ywork, st)))
-        return rc;
+      if (mixed)
+        rc = wsolve_c32(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
+                        Wr + (long)j * n_occ, (long)nr * n_occ, wsc, st);
+      else
+        rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
+                                 Wr + (long)j * n_occ, (long)nr * n_occ, f.ywork, st);
+      if (rc) return rc;
     }
   }
   ProfScope ps(ctx, PROF_THIELE, st);
@@ -360,7 +377,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   const int ns = sys->n_states;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
   size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<cplx>(n, ns) + sizeof(cplx) * (ns + 2) + 2048;
-  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov);
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns);
   cdwac_status rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
@@ -369,6 +386,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   cplx* zdev = ar.take<cplx>(1);
   cplx* Wv = ar.take<cplx>(ns);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
+  void* wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns)) : nullptr;
   if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
   if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
   for (size_t j = 0; j < omega.size(); ++j) {
@@ -387,11 +405,14 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
       if (rc) return rc;
       if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
       // column m of every state's O_n
-      if ((rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n,
-                                    sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + m)
-                                                              : (const void*)((const float*)sys->O_n + m),
-                                    sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1, f.ywork, st)))
-        return rc;
+      const void* Om = sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + m)
+                                                 : (const void*)((const float*)sys->O_n + m);
+      if (mixed)
+        rc = wsolve_c32(ctx, f.A, f.dinv, f.linv, n, Om, sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1, wsc, st);
+      else
+        rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, Om, sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1,
+                                 f.ywork, st);
+      if (rc) return rc;
       add_residue_kernel<<<1, 32 * ((ns + 31) / 32), 0, st>>>(reinterpret_cast<cplx*>(sigma), n_omega_stride,
                                                               (int)j + j_offset, ns, fm, Wv, 1);
       CDWAC_LAUNCH_CHECK(ctx);

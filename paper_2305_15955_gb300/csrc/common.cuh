@@ -5,6 +5,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -32,6 +33,9 @@ enum ProfClass {
   PROF_THIELE,
   PROF_SIGMA,
   PROF_QP,
+  PROF_LDLT_DIAG,     // fine level: the three launches of each LDL^T block step
+  PROF_LDLT_PANEL,
+  PROF_LDLT_UPDATE,
   PROF_COUNT
 };
 
@@ -50,7 +54,9 @@ struct cdwac_ctx {
   std::string last_error;
   long long launches = 0;           // kernels launched through this context
   bool quiet = false;               // set_error keeps no message (used where no allocation may happen)
-  bool prof = false;
+  int prof = 0;                     // 0 off, 1 kernel classes, 2 also the launches inside the LDL^T
+  cudaStream_t side_stream = nullptr;  // second stream of the LDL^T lookahead (joined before each call returns)
+  cudaEvent_t ev_panel = nullptr, ev_bulk = nullptr;
   std::vector<ProfRecord> prof_live;
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[PROF_COUNT] = {};
@@ -63,8 +69,8 @@ struct ProfScope {
   cudaStream_t st;
   int cls;
   cudaEvent_t stop = nullptr;
-  ProfScope(cdwac_ctx* c, int k, cudaStream_t s) : ctx(c), st(s), cls(k) {
-    if (!ctx->prof) return;
+  ProfScope(cdwac_ctx* c, int k, cudaStream_t s, int level = 1) : ctx(c), st(s), cls(k) {
+    if (ctx->prof < level) return;
     cudaEvent_t a = take(), b = take();
     cudaEventRecord(a, st);
     ctx->prof_live.push_back({cls, a, b});
@@ -216,6 +222,16 @@ size_t quadform_scratch_elems(int n, int n_cols);
 cdwac_status ldlt_quadform_pi(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv_blocks, int n,
                               const void* O, int dtype, const double* V, long o_state_stride, long ld_o, int n_states,
                               int cols_per_state, double* W_out, long w_state_stride, double* ywork, cudaStream_t st);
+// wsolve32.cu: mixed-precision W = sum_P y u / d (y = L^-1 o, u = L^-1 Pi o in FP32), Pi from negpi32 (-Pi lower, FP32)
+size_t wsolve32_scratch_bytes(int n, int n_cols);
+cdwac_status wsolve32(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
+                      int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,
+                      int cols_per_state, double* W_out, long w_state_stride, void* scratch, cudaStream_t st);
+// complex symmetric case (near-real points, residues), mixed path: W = sum y^2 / d - sum o^2 in FP32 complex
+size_t wsolve_c32_scratch_bytes(int n, int n_cols);
+cdwac_status wsolve_c32(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const cplx* linv, int n, const void* O,
+                        int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, cplx* W_out,
+                        long w_state_stride, void* scratch, cudaStream_t st);
 // thiele.cu
 cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_imag, int n_real, const double* xi,
                                const double* W_imag, int n_basis, const double* z_real, const double* W_real,

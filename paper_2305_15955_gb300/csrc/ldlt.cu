@@ -28,20 +28,30 @@ __device__ inline double ld_as<double>(const void* p, int dtype, long idx) {
   return dtype == CDWAC_F64 ? ((const double*)p)[idx] : (double)((const float*)p)[idx];
 }
 
+__device__ inline double shfl_xor_T(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ inline cplx shfl_xor_T(cplx v, int m) {
+  return mkc(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
+}
+
 __device__ inline bool bad_pivot(double d) { return !(d > 0.0); }
 __device__ inline bool bad_pivot(cplx d) { return !(hypot(d.x, d.y) > 1e-300); }
 __device__ inline unsigned pivot_err(double) { return DEV_ERR_NOT_SPD; }
 __device__ inline unsigned pivot_err(cplx) { return DEV_ERR_SINGULAR; }
 
 // ---- diagonal block --------------------------------------------------------------------------------------
+// One CTA (256 threads as 16 x 16) factors the NB x NB block held in shared memory: step j scales column j by
+// the reciprocal pivot (one division per thread per step) and updates the trailing triangle with l_i * u_k
+// (u = the unscaled column).  The unit-lower inverse X = L_kk^-1 is then built row by row, four threads per
+// column sharing each dot product.
 template <class T>
 __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv, T* linv, unsigned* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);            // [NB][NB]
   T* X = S + NB * NB;                                // [NB][NB] inverse of unit-lower L_kk
+  __shared__ T lcol[NB], ucol[NB];
   using N = Num<T>;
   const int nb = min(NB, n - k0);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   for (int e = tid; e < NB * NB; e += blockDim.x) {
     int i = e / NB, j = e % NB;
     S[e] = (i < nb && j <= i) ? A[(long)(k0 + i) * n + (k0 + j)] : (i == j ? N::one() : N::zero());
@@ -50,35 +60,42 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
   for (int j = 0; j < nb; ++j) {
     T d = S[j * NB + j];
     const bool bad = bad_pivot(d);                   // same value in every thread
-    __syncthreads();                                 // every thread has read the pivot
-    if (bad) {
-      d = N::one();
-      if (tid == 0) {
+    if (bad) d = N::one();
+    const T rinv = N::div(N::one(), d);
+    for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
+      const T u = S[i * NB + j];
+      ucol[i] = u;
+      lcol[i] = N::mul(u, rinv);
+    }
+    __syncthreads();                                 // every thread has read the pivot; l and u are ready
+    if (tid == 0) {
+      if (bad) {
         raise_status(status, pivot_err(S[j * NB + j]));
         S[j * NB + j] = N::one();
       }
-      __syncthreads();
     }
-    // a_ik -= a_ij a_kj / d for j < k <= i < nb  (uses the unscaled column j)
-    const int m = nb - j - 1;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      int i = j + 1 + e / m, k = j + 1 + e % m;
-      if (k <= i) S[i * NB + k] = N::fms(N::div(S[i * NB + j], d), S[k * NB + j], S[i * NB + k]);
+    for (int i = j + 1 + ty; i < nb; i += 16) {
+      const T li = lcol[i];
+      for (int k = j + 1 + tx; k <= i; k += 16) S[i * NB + k] = N::fms(li, ucol[k], S[i * NB + k]);
+      if (tx == 0) S[i * NB + j] = li;
     }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) S[i * NB + j] = N::div(S[i * NB + j], d);
     __syncthreads();
   }
-  // X = L_kk^{-1}, column c by thread c: X[c][c] = 1, X[i][c] = -sum_{c <= t < i} L[i][t] X[t][c]
-  for (int c = tid; c < NB; c += blockDim.x) {
-    for (int i = 0; i < NB; ++i) X[i * NB + c] = N::zero();
-    if (c < nb) {
-      X[c * NB + c] = N::one();
-      for (int i = c + 1; i < nb; ++i) {
-        T s = N::zero();
-        for (int t = c; t < i; ++t) s = N::fma_(S[i * NB + t], X[t * NB + c], s);
-        X[i * NB + c] = N::sub(N::zero(), s);
-      }
+  // X = L_kk^{-1}: X[c][c] = 1, X[i][c] = -sum_{c <= t < i} L[i][t] X[t][c]; thread (c, part) sums t = c + part mod 4
+  {
+    const int c = tid / 4, part = tid % 4;
+    for (int i = 0; i < NB; ++i)
+      if (part == 0) X[i * NB + c] = (i == c && c < nb) ? N::one() : N::zero();
+    __syncwarp();
+    for (int i = 1; i < nb; ++i) {                  // uniform trip count: the shuffles need the whole warp
+      const bool active = c < i;
+      T s = N::zero();
+      if (active)
+        for (int t = c + part; t < i; t += 4) s = N::fma_(S[i * NB + t], X[t * NB + c], s);
+      s = N::add(s, shfl_xor_T(s, 1));
+      s = N::add(s, shfl_xor_T(s, 2));
+      if (active && part == 0) X[i * NB + c] = N::sub(N::zero(), s);
+      __syncwarp();
     }
   }
   __syncthreads();
@@ -91,55 +108,45 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
   for (int i = tid; i < nb; i += blockDim.x) dinv[k0 + i] = N::div(N::one(), S[i * NB + i]);
 }
 
-// ---- panel: W_i = A_i L_kk^-T, L_i = W_i D^-1 for the 64-row block of rows below the diagonal block ------
+// ---- panel: W_i = A_i L_kk^-T, L_i = W_i D^-1 for 16 rows below the diagonal block per CTA ---------------
 template <class T>
 __global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int k0, const T* dinv, const T* linv, T* wpanel) {
-  __shared__ T Xs[TK][TP];       // chunk of L_kk^-1 rows [j][c]: Xs[c - c0][j]
-  __shared__ T As[TK][TP];       // chunk of A panel: As[c - c0][r]
+  __shared__ T Xs[TK][TP];       // chunk of (L_kk^-1)^T: Xs[c - c0][j] = Linv[j][c]
+  __shared__ T As[TK][17];       // chunk of the panel rows: As[c - c0][r]
   using N = Num<T>;
   const int nb = min(NB, n - k0);
-  const int r0 = k0 + NB + blockIdx.x * 64;
+  const int r0 = k0 + NB + blockIdx.x * 16;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int kb = k0 / NB;
-  T acc[4][4];
+  T acc[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = N::zero();
+  for (int j = 0; j < 4; ++j) acc[j] = N::zero();
   for (int c0 = 0; c0 < nb; c0 += TK) {
-    for (int e = tid; e < TK * 64; e += 256) {
-      int cc = e % TK, r = e / TK;
-      int c = c0 + cc;
-      int row = r0 + r;
+    {
+      const int cc = tid % TK, r = tid / TK;       // 256 threads = 16 rows x 16 columns of the chunk
+      const int c = c0 + cc, row = r0 + r;
       As[cc][r] = (row < n && c < nb) ? A[(long)row * n + k0 + c] : N::zero();
-      // (L^-T)[c][j] = Linv[j][c]
-      Xs[cc][r] = (c < nb) ? linv[(long)kb * NB * NB + (long)r * NB + c] : N::zero();
+    }
+    for (int e = tid; e < TK * 64; e += 256) {
+      const int cc = e % TK, j = e / TK, c = c0 + cc;
+      Xs[cc][j] = (c < nb) ? linv[(long)kb * NB * NB + (long)j * NB + c] : N::zero();
     }
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < TK; ++q) {
-      T a[4], b[4];
+      const T a = As[q][ty];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[q][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Xs[q][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = N::fma_(a[i], b[j], acc[i][j]);
+      for (int j = 0; j < 4; ++j) acc[j] = N::fma_(a, Xs[q][tx * 4 + j], acc[j]);
     }
     __syncthreads();
   }
+  const int row = r0 + ty;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int row = r0 + ty * 4 + i;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      int c = tx * 4 + j;
-      if (row < n && c < nb) {
-        wpanel[(long)row * NB + c] = acc[i][j];
-        A[(long)row * n + k0 + c] = N::mul(acc[i][j], dinv[k0 + c]);
-      }
+  for (int j = 0; j < 4; ++j) {
+    const int c = tx * 4 + j;
+    if (row < n && c < nb) {
+      wpanel[(long)row * NB + c] = acc[j];
+      A[(long)row * n + k0 + c] = N::mul(acc[j], dinv[k0 + c]);
     }
   }
 }
@@ -153,15 +160,26 @@ __device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
 }
 
 // ---- trailing update: A_ij -= W_i L_j^T over the lower triangle of rows/cols >= k1 -----------------------
+// part 0: every lower tile of the trailing matrix; part 1: its first block column only (the next panel);
+// part 2: every lower tile except the first block column.
 template <class T>
-__global__ void __launch_bounds__(256) update_kernel(T* A, int n, int k0, const T* wpanel) {
+__global__ void __launch_bounds__(256) update_kernel(T* A, int n, int k0, const T* wpanel, int part) {
   __shared__ T Ws[TK][TP];
   __shared__ T Ls[TK][TP];
   using N = Num<T>;
   const int nb = min(NB, n - k0);
   const int k1 = k0 + NB;
   int ti, tj;
-  lower_tile_coords(blockIdx.x, ti, tj);
+  if (part == 1) {
+    ti = blockIdx.x;
+    tj = 0;
+  } else {
+    lower_tile_coords(blockIdx.x, ti, tj);
+    if (part == 2) {
+      ++ti;
+      ++tj;
+    }
+  }
   const int row0 = k1 + ti * 64, col0 = k1 + tj * 64;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   T acc[4][4];
@@ -433,22 +451,82 @@ cdwac_status ldlt_quadform_pi(cdwac_ctx* ctx, const double* L, const double* din
 template <class T>
 size_t ldlt_scratch_elems(int n) {
   int nblk = (n + NB - 1) / NB;
-  return (size_t)n /*dinv*/ + (size_t)nblk * NB * NB /*linv*/ + (size_t)(nblk + 1) * NB * NB /*wpanel rows*/;
+  return (size_t)n /*dinv*/ + (size_t)nblk * NB * NB /*linv*/ + 2 * (size_t)(nblk + 1) * NB * NB /*2 panels*/;
+}
+
+// Lookahead schedule on two streams (when the context owns a side stream): after panel k, the caller's stream
+// updates only the next block column, factors the next diagonal block and builds the next panel, while the side
+// stream updates the rest of the trailing matrix; the following step waits for both.  The panel buffer is
+// double-buffered because the side stream still reads panel k while panel k+1 is written.
+template <class T>
+static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel,
+                                          cudaStream_t st, size_t dsmem) {
+  const int nblk = (n + NB - 1) / NB;
+  T* wp[2] = {wpanel, wpanel + (size_t)(nblk + 1) * NB * NB};
+  cudaStream_t side = ctx->side_stream;
+  {
+    ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
+    diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, 0, dinv, linv_blocks, ctx->d_status);
+    CDWAC_LAUNCH_CHECK(ctx);
+  }
+  // Step kb: panel kb (overlaps the side stream's update kb-1), then wait for that update (it touched block
+  // column kb+1), hand the bulk of update kb to the side stream, and update column kb+1 / factor block kb+1 here.
+  bool bulk_pending = false;
+  for (int kb = 0; kb < nblk - 1; ++kb) {
+    const int k0 = kb * NB, rest = n - (k0 + NB), m = ceil_div(rest, 64);
+    T* w = wp[kb & 1];
+    {
+      ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
+      panel_kernel<T><<<ceil_div(rest, 16), 256, 0, st>>>(A, n, k0, dinv, linv_blocks, w);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
+    if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
+    bulk_pending = false;
+    if (m > 1) {
+      CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_panel, st));
+      CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_panel, 0));
+      update_kernel<T><<<m * (m - 1) / 2, 256, 0, side>>>(A, n, k0, w, 2);
+      CDWAC_LAUNCH_CHECK(ctx);
+      CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_bulk, side));
+      bulk_pending = true;
+    }
+    {
+      ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
+      update_kernel<T><<<m, 256, 0, st>>>(A, n, k0, w, 1);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
+    {
+      ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
+      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0 + NB, dinv, linv_blocks, ctx->d_status);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
+  }
+  if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
+  return CDWAC_OK;
 }
 
 template <class T>
 cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st) {
   const size_t dsmem = 2 * NB * NB * sizeof(T);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+  if (ctx->side_stream && ctx->ev_panel && ctx->ev_bulk)
+    return ldlt_factor_lookahead<T>(ctx, A, n, dinv, linv_blocks, wpanel, st, dsmem);
   for (int k0 = 0; k0 < n; k0 += NB) {
-    diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0, dinv, linv_blocks, ctx->d_status);
-    CDWAC_LAUNCH_CHECK(ctx);
+    {
+      ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
+      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0, dinv, linv_blocks, ctx->d_status);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
     int rest = n - (k0 + NB);
     if (rest <= 0) break;
     int rblk = ceil_div(rest, 64);
-    panel_kernel<T><<<rblk, 256, 0, st>>>(A, n, k0, dinv, linv_blocks, wpanel);
-    CDWAC_LAUNCH_CHECK(ctx);
-    update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel);
+    {
+      ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
+      panel_kernel<T><<<ceil_div(rest, 16), 256, 0, st>>>(A, n, k0, dinv, linv_blocks, wpanel);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
+    ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
+    update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel, 0);
     CDWAC_LAUNCH_CHECK(ctx);
   }
   return CDWAC_OK;

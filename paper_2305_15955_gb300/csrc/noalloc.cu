@@ -43,7 +43,7 @@ extern "C" cdwac_status cdwac_build_W_imag_noalloc(const cdwac_system* sys, cons
   probe.take<double>((size_t)n * n);                             // A = I - Pi (and -Pi above the diagonal)
   probe.take<double>(n);                                         // D^-1
   probe.take<double>((size_t)nblk * 64 * 64);                    // inverses of the diagonal blocks
-  probe.take<double>((size_t)(nblk + 1) * 64 * 64);              // panel
+  probe.take<double>(2 * (size_t)(nblk + 1) * 64 * 64);          // panels
   probe.take<double>(2 * quadform_scratch_elems<double>(n, cols));  // solve vectors
   probe.take<double>(n);                                         // diagonal of Pi
   probe.take<double>((size_t)sys->n_states * n * nb);            // Pi O
@@ -69,7 +69,7 @@ extern "C" cdwac_status cdwac_build_W_imag_noalloc(const cdwac_system* sys, cons
   double* A = ar.take<double>((size_t)n * n);
   double* dinv = ar.take<double>(n);
   double* linv = ar.take<double>((size_t)nblk * 64 * 64);
-  double* wpanel = ar.take<double>((size_t)(nblk + 1) * 64 * 64);
+  double* wpanel = ar.take<double>(2 * (size_t)(nblk + 1) * 64 * 64);
   double* ywork = ar.take<double>(2 * quadform_scratch_elems<double>(n, cols));
   double* pidiag = ar.take<double>(n);
   double* V = ar.take<double>((size_t)sys->n_states * n * nb);

@@ -134,7 +134,7 @@ struct Cfg {
 // A = I + S B^T (lower triangle).  NACC == 1: real A (double*).  NACC == 2: complex A (cplx*), re from S0, im from S1.
 template <int NACC>
 __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
-                                                         void* A_out, unsigned* status) {
+                                                         void* A_out, float* negpi32, unsigned* status) {
   using C = Cfg<NACC>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -256,6 +256,18 @@ __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__
           for (int j = 0; j < 32; ++j) {
             const int col = col0 + j;
             if (col <= row && col < n) Ar[col] = (col == row ? 1.0 : 0.0) + (double)__uint_as_float(v0[j]);
+          }
+          if (negpi32) {   // -Pi in FP32, both triangles, for the Pi O product of the W solves
+            float* Pr = negpi32 + (long)row * n;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = col0 + j;
+              if (col <= row && col < n) {
+                Pr[col] = __uint_as_float(v0[j]);
+                // transposed entry: the 32 lanes hold consecutive rows, so this store is coalesced
+                if (col < row) negpi32[(long)col * n + row] = __uint_as_float(v0[j]);
+              }
+            }
           }
         } else {
           cplx* Ac = reinterpret_cast<cplx*>(A_out) + (long)row * n;
@@ -424,7 +436,7 @@ int elementwise_blocks(cdwac_ctx* ctx, long work) {
 }
 
 template <int NACC>
-cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, cudaStream_t st) {
+cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, float* negpi32, cudaStream_t st) {
   using C = Cfg<NACC>;
   Maps maps;
   memset(&maps, 0, sizeof(maps));
@@ -434,7 +446,8 @@ cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, cudaStre
   if (!ok) return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel<NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const int nt = (n + BM - 1) / BM;
-  tc_syrk_kernel<NACC><<<nt * (nt + 1) / 2, 128, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, ctx->d_status);
+  tc_syrk_kernel<NACC><<<nt * (nt + 1) / 2, 128, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, negpi32,
+                                                                  ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }
@@ -484,7 +497,7 @@ static cdwac_status scale(cdwac_ctx* ctx, const Scratch& s, const void* O_ia, in
 }
 
 cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
-                        long n_ov, const double* xi_dev, double* A, cudaStream_t st) {
+                        long n_ov, const double* xi_dev, double* A, float* negpi32, cudaStream_t st) {
   Scratch s = carve(scratch, n_aux, n_ov);
   cdwac_status rc;
   {
@@ -493,7 +506,7 @@ cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dty
   }
   if (rc) return rc;
   ProfScope ps(ctx, PROF_PI_TC_IMAG, st);
-  return run_syrk<1>(ctx, s, n_aux, A, st);
+  return run_syrk<1>(ctx, s, n_aux, A, negpi32, st);
 }
 
 cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
@@ -506,5 +519,5 @@ cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int 
   }
   if (rc) return rc;
   ProfScope ps(ctx, PROF_PI_TC_CPLX, st);
-  return run_syrk<2>(ctx, s, n_aux, A, st);
+  return run_syrk<2>(ctx, s, n_aux, A, nullptr, st);
 }

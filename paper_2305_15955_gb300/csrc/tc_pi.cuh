@@ -9,9 +9,10 @@ size_t tc_pi_scratch_bytes(int n_aux, long n_ov);
 cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void* O_ia, int dtype, int n_aux, long n_ov, void* scratch,
                            cudaStream_t st);
 // A = I - Pi(i xi) (real, lower triangle), xi read from xi_dev[0].  O_ia is the source of the planes built by
-// tc_pi_prepare (its weighted copy is re-split for every frequency).
+// tc_pi_prepare (its weighted copy is re-split for every frequency).  If negpi32 is not null it receives -Pi in
+// FP32 (the full symmetric matrix, row-major [n_aux][n_aux]).
 cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
-                        long n_ov, const double* xi_dev, double* A, cudaStream_t st);
+                        long n_ov, const double* xi_dev, double* A, float* negpi32, cudaStream_t st);
 // A = I - Pi(z) (complex, lower triangle), z read from z_dev[0].
 cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
                            long n_ov, const cplx* z_dev, cplx* A, cudaStream_t st);
