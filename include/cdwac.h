@@ -187,6 +187,44 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
+/* ---- batched launch ------------------------------------------------------------------------------------ */
+
+/* One system of a batch and its outputs (all device pointers; layouts as in the single-system calls). */
+typedef struct {
+  cdwac_system sys;
+  double* xi;            /* [n_imag] */
+  double* wxi;           /* [n_imag] */
+  double* W_imag;        /* [n_states][n_imag][n_basis] */
+  double* z_real;        /* [n_states][n_real][2] or NULL */
+  double* W_real;        /* [n_states][n_real][n_occ][2] or NULL */
+  cdwac_pade pade;       /* fits of this system (arrays sized for it) */
+  const double* omega;   /* [n_omega] Sigma grid (n_omega may be 0) */
+  int n_omega;
+  double* sigma;         /* [n_states][n_omega][2] */
+  const double* shift;   /* [n_states] or NULL */
+  const double* qp_grid; /* [n_grid] bracketing grid of the QP fallback */
+  int n_grid;
+  double* e_qp;          /* [n_states] */
+  double* Z;             /* [n_states] */
+  int* iters;            /* [n_states] */
+  int* qp_status;        /* [n_states] */
+} cdwac_batch_item;
+
+#define CDWAC_BATCH_GRAPH 1u     /* capture the whole batch into one CUDA graph and replay it */
+#define CDWAC_BATCH_AUTOTUNE 2u  /* choose lanes and LDL^T lookahead by timing candidates (cached per size bucket) */
+
+/* CD-WAC for many systems of uneven size in one stream-ordered call: the systems are spread over up to
+ * `max_lanes` concurrent lanes (streams with their own scratch), largest first, and each runs W(i xi), the
+ * near-real points, the Thiele fits, Sigma on its grid and the QP equation.  With CDWAC_BATCH_GRAPH the batch is
+ * captured once into a CUDA graph (keyed on the item array's contents) and later calls with the same items
+ * replay it: the items' buffers must stay valid.  With CDWAC_BATCH_AUTOTUNE the first call for a size bucket
+ * times every lane count in {1, 2, 4, 8} <= max_lanes with and without the LDL^T lookahead and keeps the fastest;
+ * choices are appended to the file named by the environment variable CDWAC_TUNE_CACHE (if set) and read back by
+ * later processes.  `chosen` (may be NULL) receives {lanes, lookahead}.  The precision and parameters are the
+ * same for every item. */
+cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items, const cdwac_params* prm,
+                             double tol, int max_iter, int max_lanes, unsigned flags, int* chosen, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------------------------------ */
 
 /* Fixed device scratch of cdwac_build_W_imag_noalloc (held by every GPU that loads the library). */

@@ -377,13 +377,14 @@ class QPResult:
     status: int            # 0 converged by fixed point, 1 by bracketed bisection, 2 not converged
 
 
-def qp_solve(sigma_fn, eps_n, shift, omega_grid, tol=1e-7, max_iter=100, h=1e-5, bisect_tol=1e-9):
+def qp_solve(sigma_fn, eps_n, shift, omega_grid, tol=1e-7, max_iter=100, h=1e-5, bisect_tol=1e-9, upper=np.inf):
     """Solve e = eps_n + shift + Re Sigma^c_n(e) (Eq. qp_eq with shift = Sigma^x_n - v^xc_n).
 
     Fixed-point iteration from eps_n until |e_new - e| < tol.  If it does not converge, every sign change of
     f(w) = w - eps_n - shift - Re Sigma(w) between neighbouring points of omega_grid is bisected to bisect_tol;
     roots with |f| < 1e-6 are kept and the one with the largest Z in (0, 1] is returned.
-    Z = 1 / (1 - d Re Sigma / d w) by a central difference of step h.
+    Z = 1 / (1 - d Re Sigma / d w) by a central difference of step h.  An iterate at or above `upper` (for CD-WAC
+    the LUMO: the continuation covers occupied residues only) ends the fixed point as not converged.
     """
     def zfac(e):
         d = (sigma_fn(e + h).real - sigma_fn(e - h).real) / (2.0 * h)
@@ -392,6 +393,8 @@ def qp_solve(sigma_fn, eps_n, shift, omega_grid, tol=1e-7, max_iter=100, h=1e-5,
     e = eps_n
     for it in range(1, max_iter + 1):
         e_new = eps_n + shift + sigma_fn(e).real
+        if not e_new < upper:
+            break
         if abs(e_new - e) < tol:
             return QPResult(e_new, zfac(e_new), it, 0)
         e = e_new
@@ -485,7 +488,7 @@ def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=N
         sig = lambda w, s=s, model=model: sigma_c_wac(model, Wim[s], eps, n_occ, xi, wxi, w, params.eta)
         sh = 0.0 if shifts is None else shifts[s]
         res = {"n": n, "z_real": zr, "W_real": Wre, "model": model,
-               "qp": qp_solve(sig, eps[n], sh, omega_grid)}
+               "qp": qp_solve(sig, eps[n], sh, omega_grid, upper=eps[n_occ])}
         if with_sigma:
             res["sigma"] = np.array([sig(w) for w in omega_grid])
         out["states"].append(res)

@@ -26,7 +26,9 @@ PREC_FP64, PREC_MIXED = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
-            "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count", "cdwac_build_W_imag_noalloc"]
+            "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count", "cdwac_build_W_imag_noalloc",
+            "cdwac_batch_run"]
+BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -57,6 +59,15 @@ class _Pade(ctypes.Structure):
     _fields_ = [("n_states", ctypes.c_int), ("n_occ", ctypes.c_int), ("M", ctypes.c_int),
                 ("a", ctypes.c_void_p), ("z2", ctypes.c_void_p), ("nodes", ctypes.c_void_p),
                 ("n_used", ctypes.c_void_p)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("sys", _System), ("xi", ctypes.c_void_p), ("wxi", ctypes.c_void_p), ("W_imag", ctypes.c_void_p),
+                ("z_real", ctypes.c_void_p), ("W_real", ctypes.c_void_p), ("pade", _Pade),
+                ("omega", ctypes.c_void_p), ("n_omega", ctypes.c_int), ("sigma", ctypes.c_void_p),
+                ("shift", ctypes.c_void_p), ("qp_grid", ctypes.c_void_p), ("n_grid", ctypes.c_int),
+                ("e_qp", ctypes.c_void_p), ("Z", ctypes.c_void_p), ("iters", ctypes.c_void_p),
+                ("qp_status", ctypes.c_void_p)]
 
 
 def library_path() -> str:
@@ -94,6 +105,8 @@ def load():
     lib.cdwac_launch_count.argtypes = [P]
     lib.cdwac_launch_count.restype = ctypes.c_longlong
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
+    lib.cdwac_batch_run.argtypes = [P, ctypes.POINTER(_BatchItem), ctypes.c_int, prmp, ctypes.c_double, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_uint, ctypes.POINTER(ctypes.c_int), P]
     _lib = lib
     return lib
 
@@ -293,6 +306,54 @@ class Context:
         if sync:
             self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
         return e, Z, it, qs
+
+
+class BatchResult:
+    """Device outputs of one system of a batch (same layouts as the single-system calls)."""
+
+    def __init__(self, system: System, params: Params, omega, qp_grid, dev):
+        ns, nb, no = system.n_states, system.n_basis, system.n_occ
+        self.system = system
+        self.xi = torch.empty(params.n_imag, dtype=torch.float64, device=dev)
+        self.wxi = torch.empty_like(self.xi)
+        self.W_imag = torch.empty(ns, params.n_imag, nb, dtype=torch.float64, device=dev)
+        nr = max(params.n_real, 1)
+        self.pade = PadeModel(a=torch.zeros(ns, no, params.pade_M, dtype=torch.complex128, device=dev),
+                              z2=torch.zeros(ns, no, params.pade_M, dtype=torch.complex128, device=dev),
+                              nodes=torch.full((ns, no, params.pade_M), -1, dtype=torch.int32, device=dev),
+                              n_used=torch.zeros(ns, no, dtype=torch.int32, device=dev),
+                              z_real=torch.zeros(ns, nr, dtype=torch.complex128, device=dev),
+                              W_real=torch.zeros(ns, nr, no, dtype=torch.complex128, device=dev), M=params.pade_M)
+        self.omega = torch.as_tensor(omega, dtype=torch.float64).to(dev).contiguous()
+        self.sigma = torch.empty(ns, self.omega.numel(), dtype=torch.complex128, device=dev)
+        self.qp_grid = torch.as_tensor(qp_grid, dtype=torch.float64).to(dev).contiguous()
+        self.e_qp = torch.empty(ns, dtype=torch.float64, device=dev)
+        self.Z = torch.empty_like(self.e_qp)
+        self.iters = torch.empty(ns, dtype=torch.int32, device=dev)
+        self.qp_status = torch.empty_like(self.iters)
+
+    def c(self) -> _BatchItem:
+        return _BatchItem(self.system.c, self.xi.data_ptr(), self.wxi.data_ptr(), self.W_imag.data_ptr(),
+                          self.pade.z_real.data_ptr(), self.pade.W_real.data_ptr(), self.pade.c(),
+                          self.omega.data_ptr(), int(self.omega.numel()), self.sigma.data_ptr(), None,
+                          self.qp_grid.data_ptr(), int(self.qp_grid.numel()), self.e_qp.data_ptr(),
+                          self.Z.data_ptr(), self.iters.data_ptr(), self.qp_status.data_ptr())
+
+
+def batch_run(ctx: "Context", results, params: Params, max_lanes=4, graph=False, autotune=False, tol=1e-7,
+              max_iter=100, sync=True, items=None):
+    """cdwac_batch_run over BatchResult objects; returns (lanes, lookahead) the call used and the ctypes items
+    (pass them back as `items` to replay a captured graph with the identical item array)."""
+    if items is None:
+        items = (_BatchItem * len(results))(*[r.c() for r in results])
+    p = params.c()
+    chosen = (ctypes.c_int * 2)()
+    flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+    ctx._check(ctx.lib.cdwac_batch_run(ctx.h, items, len(results), ctypes.byref(p), float(tol), int(max_iter),
+                                       int(max_lanes), flags, chosen, ctx._stream()))
+    if sync:
+        ctx.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
+    return (int(chosen[0]), int(chosen[1])), items
 
 
 def build_W_imag_noalloc(system: System, params: Params, xi, wxi, W_imag, dev_status=None, stream=None) -> int:

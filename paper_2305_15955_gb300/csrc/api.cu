@@ -39,6 +39,7 @@ cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes) {
     return set_error(ctx, CDWAC_ERR_OOM, "scratch allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
   }
   ctx->scratch_bytes = want;
+  ++ctx->scratch_gen;
   return CDWAC_OK;
 }
 
@@ -64,12 +65,13 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
     return CDWAC_ERR_UNSUPPORTED;
   }
   ctx->num_sms = p.multiProcessorCount;
-  if (cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+  if (cudaStreamCreateWithFlags(&ctx->own_side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_bulk, cudaEventDisableTiming) != cudaSuccess) {
     delete ctx;
     return CDWAC_ERR_CUDA;
   }
+  ctx->side_stream = ctx->own_side;
   if (cudaMalloc(&ctx->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess) {
@@ -121,6 +123,11 @@ long long cdwac_launch_count(const cdwac_ctx* ctx) { return ctx ? ctx->launches 
 void cdwac_destroy(cdwac_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  for (auto* l : ctx->lanes) cdwac_destroy(l);
+  for (auto s : ctx->lane_streams) cudaStreamDestroy(s);
+  for (auto e : ctx->lane_events) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
   for (auto& r : ctx->prof_live) {
     cudaEventDestroy(r.start);
     cudaEventDestroy(r.stop);
@@ -128,10 +135,12 @@ void cdwac_destroy(cdwac_ctx* ctx) {
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->ev_panel) cudaEventDestroy(ctx->ev_panel);
   if (ctx->ev_bulk) cudaEventDestroy(ctx->ev_bulk);
-  if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+  if (ctx->own_side) cudaStreamDestroy(ctx->own_side);
   if (ctx->scratch) cudaFree(ctx->scratch);
-  if (ctx->d_status) cudaFree(ctx->d_status);
-  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (!ctx->is_lane) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  }
   delete ctx;
 }
 

@@ -51,12 +51,22 @@ struct cdwac_ctx {
   unsigned* h_status = nullptr;     // pinned mirror
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  unsigned long long scratch_gen = 0;   // bumped whenever the scratch is reallocated (invalidates captured graphs)
   std::string last_error;
   long long launches = 0;           // kernels launched through this context
   bool quiet = false;               // set_error keeps no message (used where no allocation may happen)
   int prof = 0;                     // 0 off, 1 kernel classes, 2 also the launches inside the LDL^T
   cudaStream_t side_stream = nullptr;  // second stream of the LDL^T lookahead (joined before each call returns)
+  cudaStream_t own_side = nullptr;     // the side stream this context created (side_stream may be switched off)
   cudaEvent_t ev_panel = nullptr, ev_bulk = nullptr;
+  // batched launch: lane contexts (own scratch and streams, shared status word), fork/join events, graph cache
+  bool is_lane = false;
+  std::vector<cdwac_ctx*> lanes;
+  std::vector<cudaStream_t> lane_streams;
+  std::vector<cudaEvent_t> lane_events;
+  cudaEvent_t ev_fork = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::string graph_key;
   std::vector<ProfRecord> prof_live;
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[PROF_COUNT] = {};

@@ -95,7 +95,7 @@ __device__ inline cplx partial_I(const SigmaArgs& A, int s, double omega) {
 }
 
 // This thread's share of R_n(omega) from the continued fractions (occupied m).
-__device__ inline cplx partial_R_wac(const SigmaArgs& A, int s, double omega, unsigned* status) {
+__device__ inline cplx partial_R_wac(const SigmaArgs& A, int s, double omega, unsigned* status, bool report) {
   cplx acc = mkc(0.0, 0.0);
   for (int m = threadIdx.x; m < A.n_occ; m += blockDim.x) {
     const double f = -theta(A.eps[m] - omega);
@@ -113,13 +113,14 @@ __device__ inline cplx partial_R_wac(const SigmaArgs& A, int s, double omega, un
     acc = acc + f * T;
   }
   // a virtual residue (omega above a virtual level) has no continuation
-  if (threadIdx.x == 0 && omega > A.eps[A.n_occ]) raise_status(status, DEV_ERR_BOUNDS);
+  if (report && threadIdx.x == 0 && omega > A.eps[A.n_occ]) raise_status(status, DEV_ERR_BOUNDS);
   return acc;
 }
 
-__device__ inline cplx block_sigma(const SigmaArgs& A, int s, double omega, cplx* red, unsigned* status) {
+__device__ inline cplx block_sigma(const SigmaArgs& A, int s, double omega, cplx* red, unsigned* status,
+                                   bool report = true) {
   cplx v = mkc(0.0, 0.0) - partial_I(A, s, omega);
-  if (A.pa) v = v + partial_R_wac(A, s, omega, status);
+  if (A.pa) v = v + partial_R_wac(A, s, omega, status, report);
   return block_sum(v, red);
 }
 
@@ -131,7 +132,8 @@ __global__ void __launch_bounds__(SIG_THREADS) sigma_kernel(SigmaArgs A, const d
   if (threadIdx.x == 0) sigma[(long)s * n_omega + j] = v;
 }
 
-// Fixed point e <- eps_n + shift + Re Sigma(e); fallback: bisect every sign change of
+// Fixed point e <- eps_n + shift + Re Sigma(e) (for CD-WAC it stops if an iterate leaves the range below the
+// LUMO); fallback: bisect every sign change of
 // f(w) = w - eps_n - shift - Re Sigma(w) on the grid, keep roots with |f| < 1e-6 and the largest Z in (0, 1].
 __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const double* shift, const double* grid,
                                                          int n_grid, double tol, int max_iter, double* e_qp,
@@ -141,7 +143,9 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
   const double en = A.eps[A.states[s]];
   const double sh = shift ? shift[s] : 0.0;
   const double h = 1e-5;
-  auto resig = [&](double w) { return block_sigma(A, s, w, red, status).x; };
+  auto resig = [&](double w) { return block_sigma(A, s, w, red, status, false).x; };
+  // the continuation covers residues of occupied orbitals only: an iterate above the LUMO ends the fixed point
+  const double upper = A.pa ? A.eps[A.n_occ] : INFINITY;
   auto zfac = [&](double e) {
     double d = (resig(e + h) - resig(e - h)) / (2.0 * h);
     return 1.0 / (1.0 - d);
@@ -152,6 +156,7 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
   double e_new = e;
   for (it = 1; it <= max_iter; ++it) {
     e_new = en + sh + resig(e);
+    if (!(e_new < upper)) break;
     if (fabs(e_new - e) < tol) {
       conv = 1;
       break;

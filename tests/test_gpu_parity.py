@@ -132,7 +132,7 @@ def _replayed_state(ref, s, pade, p, n_occ, eps, omega):
     model_p = o.WacModel(fits=fits_p)
     sens = np.array([abs(o.sigma_c_wac(model_p, Wim, eps, n_occ, xi, wxi, w, p.eta) - v)
                      for w, v in zip(omega, sig_ref)])
-    return sig_ref, o.qp_solve(sig, eps[ref["states"][s]["n"]], 0.0, omega), sens
+    return sig_ref, o.qp_solve(sig, eps[ref["states"][s]["n"]], 0.0, omega, upper=eps[n_occ]), sens
 
 
 def _assert_sigma(sig_gpu, sig_ref, sens):
