@@ -225,6 +225,44 @@ typedef struct {
 cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items, const cdwac_params* prm,
                              double tol, int max_iter, int max_lanes, unsigned flags, int* chosen, void* stream);
 
+/* ---- learned continuation (pole-residue MLP) ----------------------------------------------------------- */
+/* Not in the paper: an alternative to the Thiele continuation in the residue term R_n (Eq. Rn_term).  A network
+ * 32 -> 3 x 256 (GELU) -> 16 maps x_k = W_nm(i xi_{3k}) / s (k < 32, s = |W_nm(i xi_1)|) to 8 poles
+ * Omega_s = softplus(o_s) + 0.05 Ha and residues r_s = softplus(o_{8+s}); the model is the sum-over-poles form of W
+ * behind Eq. sigma_pole, W(z) = -s sum_s r_s 2 Omega_s / (Omega_s^2 - z^2) (<= 0 on the imaginary axis). */
+#define CDWAC_MLP_IN 32
+#define CDWAC_MLP_HIDDEN 256
+#define CDWAC_MLP_POLES 8
+/* FP32 parameters, per layer row-major weights [in][out] then bias: 32x256,256 | 256x256,256 | 256x256,256 | 256x16,16 */
+#define CDWAC_MLP_NPARAMS (32 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 16 + 16)
+
+/* Features and training targets of every (state, occupied m) pair, b = s * n_occ + m (B = n_states * n_occ):
+ *   x [B][32] float, scale [B] float, z_ref and w_ref [B][32 + n_real][2]: the 32 imaginary nodes i xi_{3k} with
+ *   W(i xi_{3k}), then the near-real points z_real[s][j] with W_real[s][j][m] (outputs of cdwac_build_W_imag and
+ *   cdwac_fit_pade).  Needs n_imag >= 94. */
+cdwac_status cdwac_mlp_features(cdwac_ctx* ctx, const double* xi, const double* W_imag, int n_states, int n_imag,
+                                int n_basis, int n_occ, const double* z_real, const double* W_real, int n_real,
+                                float* x, float* scale, double* z_ref, double* w_ref, void* stream);
+/* One training gradient (FP32): loss = mean_b (1/J) sum_j |W_model(z_j) - w_ref_j|^2 / (scale_b^2 + |w_ref_j|^2)
+ * (written to *loss, a device double) and its gradient with respect to params (grad [CDWAC_MLP_NPARAMS] float). */
+cdwac_status cdwac_mlp_loss_grad(cdwac_ctx* ctx, const float* params, int batch, const float* x, const float* scale,
+                                 int n_ref, const double* z_ref, const double* w_ref, float* grad, double* loss,
+                                 void* stream);
+/* Adam step on params with moments m, v (all [CDWAC_MLP_NPARAMS] float); step counts from 1. */
+cdwac_status cdwac_mlp_adam(cdwac_ctx* ctx, float* params, const float* grad, float* m, float* v, int step, float lr,
+                            float beta1, float beta2, float eps, void* stream);
+/* Inference with BF16 copies of the weights: poles [batch][8][2] = (Omega_s, r_s * scale) in Ha. */
+cdwac_status cdwac_mlp_poles(cdwac_ctx* ctx, const float* params, int batch, const float* x, const float* scale,
+                             double* poles, void* stream);
+/* cdwac_sigma / cdwac_qp_solve with the residue term from poles [n_states][n_occ][8][2] instead of Thiele fits. */
+cdwac_status cdwac_sigma_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                               const double* wxi, const double* W_imag, const double* poles, const double* omega,
+                               int n_omega, double* sigma, void* stream);
+cdwac_status cdwac_qp_solve_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                                  const double* wxi, const double* W_imag, const double* poles, const double* shift,
+                                  const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                                  int* iters, int* qp_status, void* stream);
+
 /* ---- allocation-free variant ------------------------------------------------------------------------ */
 
 /* Fixed device scratch of cdwac_build_W_imag_noalloc (held by every GPU that loads the library). */

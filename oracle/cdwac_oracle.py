@@ -359,6 +359,20 @@ def sigma_R_wac(model, eps, n_occ, omega, eta):
     return complex(R)
 
 
+def sigma_R_poles(poles_s, eps, n_occ, omega, eta):
+    """R_n(omega), Eq. Rn_term, with W_nm(z) = -sum_s r_s 2 Omega_s / (Omega_s^2 - z^2) from a pole model
+    poles_s [n_occ][n_poles][2] = (Omega_s, r_s) per occupied m (the learned continuation; not in the paper)."""
+    f = residue_factors(eps, n_occ, omega)
+    R = 0.0 + 0.0j
+    for m in np.nonzero(f)[0]:
+        if m >= n_occ:
+            raise ValueError("the pole model covers occupied residues only (omega below the LUMO)")
+        z = abs(eps[m] - omega) + 1j * eta
+        Om, r = poles_s[m, :, 0], poles_s[m, :, 1]
+        R += f[m] * np.sum(-r * 2.0 * Om / (Om * Om - z * z))
+    return complex(R)
+
+
 def sigma_c_wac(model, W_imag_s, eps, n_occ, xi, wxi, omega, eta):
     """Sigma^c_n(omega) = R_n - I_n with the continued residue term (CD-WAC)."""
     return sigma_R_wac(model, eps, n_occ, omega, eta) - sigma_I(W_imag_s, eps, n_occ, xi, wxi, omega, eta)

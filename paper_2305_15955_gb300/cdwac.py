@@ -27,7 +27,10 @@ MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
             "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count", "cdwac_build_W_imag_noalloc",
-            "cdwac_batch_run"]
+            "cdwac_batch_run", "cdwac_mlp_features", "cdwac_mlp_loss_grad", "cdwac_mlp_adam", "cdwac_mlp_poles",
+            "cdwac_sigma_poles", "cdwac_qp_solve_poles"]
+MLP_IN, MLP_HIDDEN, MLP_POLES = 32, 256, 8
+MLP_NPARAMS = 32 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 16 + 16
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -105,6 +108,15 @@ def load():
     lib.cdwac_launch_count.argtypes = [P]
     lib.cdwac_launch_count.restype = ctypes.c_longlong
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
+    lib.cdwac_mlp_features.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
+                                       ctypes.c_int, P, P, P, P, P]
+    lib.cdwac_mlp_loss_grad.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
+    lib.cdwac_mlp_adam.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, P]
+    lib.cdwac_mlp_poles.argtypes = [P, P, ctypes.c_int, P, P, P, P]
+    lib.cdwac_sigma_poles.argtypes = [P, sysp, prmp, P, P, P, P, P, ctypes.c_int, P, P]
+    lib.cdwac_qp_solve_poles.argtypes = [P, sysp, prmp, P, P, P, P, P, P, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_int, P, P, P, P, P]
     lib.cdwac_batch_run.argtypes = [P, ctypes.POINTER(_BatchItem), ctypes.c_int, prmp, ctypes.c_double, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_uint, ctypes.POINTER(ctypes.c_int), P]
     _lib = lib
@@ -236,6 +248,72 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.cdwac_launch_count(self.h))
+
+    # ---- learned continuation -------------------------------------------------------------------------
+    def mlp_features(self, xi, W_imag, n_occ, pade: PadeModel | None = None, n_real=0):
+        """x [B, 32], scale [B], z_ref, w_ref [B, 32 + n_real] for every (state, occupied m) pair."""
+        dev = self._dev()
+        ns, n_imag, nb = W_imag.shape
+        B, J = ns * n_occ, MLP_IN + n_real
+        x = torch.empty(B, MLP_IN, dtype=torch.float32, device=dev)
+        scale = torch.empty(B, dtype=torch.float32, device=dev)
+        z_ref = torch.empty(B, J, dtype=torch.complex128, device=dev)
+        w_ref = torch.empty(B, J, dtype=torch.complex128, device=dev)
+        zr = _ptr(pade.z_real) if (pade is not None and n_real > 0) else None
+        wr = _ptr(pade.W_real) if (pade is not None and n_real > 0) else None
+        self._check(self.lib.cdwac_mlp_features(self.h, _ptr(xi), _ptr(W_imag), ns, n_imag, nb, n_occ, zr, wr,
+                                                n_real, _ptr(x), _ptr(scale), _ptr(z_ref), _ptr(w_ref),
+                                                self._stream()))
+        return x, scale, z_ref, w_ref
+
+    def mlp_loss_grad(self, params, x, scale, z_ref, w_ref, grad=None, loss=None):
+        grad = torch.empty_like(params) if grad is None else grad
+        loss = torch.empty(1, dtype=torch.float64, device=params.device) if loss is None else loss
+        self._check(self.lib.cdwac_mlp_loss_grad(self.h, _ptr(params), int(x.shape[0]), _ptr(x), _ptr(scale),
+                                                 int(z_ref.shape[1]), _ptr(z_ref), _ptr(w_ref), _ptr(grad),
+                                                 _ptr(loss), self._stream()))
+        return grad, loss
+
+    def mlp_adam(self, params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self._check(self.lib.cdwac_mlp_adam(self.h, _ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step),
+                                            float(lr), float(beta1), float(beta2), float(eps), self._stream()))
+
+    def mlp_poles(self, params, x, scale):
+        poles = torch.empty(x.shape[0], MLP_POLES, 2, dtype=torch.float64, device=params.device)
+        self._check(self.lib.cdwac_mlp_poles(self.h, _ptr(params), int(x.shape[0]), _ptr(x), _ptr(scale),
+                                             _ptr(poles), self._stream()))
+        return poles
+
+    def sigma_poles(self, system: System, params: Params, xi, wxi, W_imag, poles, omega, sync=True):
+        dev = self._dev()
+        omega = torch.as_tensor(omega, dtype=torch.float64).to(dev).contiguous()
+        out = torch.empty(system.n_states, omega.numel(), dtype=torch.complex128, device=dev)
+        p = params.c()
+        self._check(self.lib.cdwac_sigma_poles(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(wxi),
+                                               _ptr(W_imag), _ptr(poles), _ptr(omega), int(omega.numel()), _ptr(out),
+                                               self._stream()))
+        if sync:
+            self.sync_status()
+        return out
+
+    def qp_solve_poles(self, system: System, params: Params, xi, wxi, W_imag, poles, omega_grid, shift=None,
+                       tol=1e-7, max_iter=100, sync=True):
+        dev = self._dev()
+        grid = torch.as_tensor(omega_grid, dtype=torch.float64).to(dev).contiguous()
+        sh = None if shift is None else torch.as_tensor(shift, dtype=torch.float64).to(dev).contiguous()
+        ns = system.n_states
+        e = torch.empty(ns, dtype=torch.float64, device=dev)
+        Z = torch.empty_like(e)
+        it = torch.empty(ns, dtype=torch.int32, device=dev)
+        qs = torch.empty_like(it)
+        p = params.c()
+        self._check(self.lib.cdwac_qp_solve_poles(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi),
+                                                  _ptr(wxi), _ptr(W_imag), _ptr(poles), _ptr(sh), _ptr(grid),
+                                                  int(grid.numel()), float(tol), int(max_iter), _ptr(e), _ptr(Z),
+                                                  _ptr(it), _ptr(qs), self._stream()))
+        if sync:
+            self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
+        return e, Z, it, qs
 
     def _dev(self):
         return torch.device("cuda", self.device)

@@ -85,7 +85,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
 
 static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",   "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
                                               "ldlt_fp64", "w_solves",  "thiele_fit", "sigma",         "qp_solve",
-                                              "ldlt_diag", "ldlt_panel", "ldlt_update"};
+                                              "mlp",       "ldlt_diag", "ldlt_panel", "ldlt_update"};
 
 void cdwac_profile_enable(cdwac_ctx* ctx, int on) {
   if (ctx) ctx->prof = on < 0 ? 0 : (on > 2 ? 2 : on);
@@ -599,3 +599,35 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
 }
 
 }  // extern "C"
+
+// ---- learned continuation in the residue term -------------------------------------------------------------
+
+extern "C" cdwac_status cdwac_sigma_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
+                                          const double* xi, const double* wxi, const double* W_imag,
+                                          const double* poles, const double* omega, int n_omega, double* sigma,
+                                          void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag || !poles || !omega || !sigma || n_omega < 0)
+    return set_error(ctx, CDWAC_ERR_ARG, "bad sigma_poles args");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (n_omega == 0) return CDWAC_OK;
+  ProfScope ps(ctx, PROF_SIGMA, (cudaStream_t)stream);
+  return launch_sigma_poles(ctx, sys, prm, xi, wxi, W_imag, poles, omega, n_omega, sigma, (cudaStream_t)stream);
+}
+
+extern "C" cdwac_status cdwac_qp_solve_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
+                                             const double* xi, const double* wxi, const double* W_imag,
+                                             const double* poles, const double* shift, const double* omega,
+                                             int n_grid, double tol, int max_iter, double* e_qp, double* Z, int* iters,
+                                             int* qp_status, void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag || !poles || !omega || n_grid < 2 || !e_qp || !Z || !iters || !qp_status ||
+      max_iter < 1 || !(tol > 0))
+    return set_error(ctx, CDWAC_ERR_ARG, "bad qp_solve_poles args");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ProfScope ps(ctx, PROF_QP, (cudaStream_t)stream);
+  return launch_qp_poles(ctx, sys, prm, xi, wxi, W_imag, poles, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters,
+                         qp_status, (cudaStream_t)stream);
+}

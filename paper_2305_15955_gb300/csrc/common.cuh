@@ -33,6 +33,7 @@ enum ProfClass {
   PROF_THIELE,
   PROF_SIGMA,
   PROF_QP,
+  PROF_MLP,           // learned continuation: training step or pole inference
   PROF_LDLT_DIAG,     // fine level: the three launches of each LDL^T block step
   PROF_LDLT_PANEL,
   PROF_LDLT_UPDATE,
@@ -256,6 +257,15 @@ cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdw
 cdwac_status launch_sigma_I_only(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
                                  const double* xi, const double* wxi, const double* W_imag, const double* omega,
                                  int n_omega, double* sigma, cudaStream_t st);
+// poles: [n_states][n_occ][CDWAC_MLP_POLES][2] (Omega, residue) of the learned continuation, replacing the Thiele
+// fits in the residue term when pade is null and poles is not.
+cdwac_status launch_sigma_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                                const double* wxi, const double* W_imag, const double* poles, const double* omega,
+                                int n_omega, double* sigma, cudaStream_t st);
+cdwac_status launch_qp_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                             const double* wxi, const double* W_imag, const double* poles, const double* shift,
+                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                             int* iters, int* qp_status, cudaStream_t st);
 cdwac_status launch_qp_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
                            const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,

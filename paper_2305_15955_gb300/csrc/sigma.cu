@@ -31,6 +31,8 @@ struct SigmaArgs {
   const cplx* pz2;
   const int* n_used;
   int M_cap;
+  // learned continuation (may be null): [n_states][n_occ][CDWAC_MLP_POLES][2] (Omega, residue)
+  const double* poles;
 };
 
 __device__ inline double theta(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); }
@@ -117,10 +119,31 @@ __device__ inline cplx partial_R_wac(const SigmaArgs& A, int s, double omega, un
   return acc;
 }
 
+// This thread's share of R_n(omega) from the learned pole model: T(z) = -sum_s r_s 2 Omega_s / (Omega_s^2 - z^2).
+__device__ inline cplx partial_R_poles(const SigmaArgs& A, int s, double omega, unsigned* status, bool report) {
+  cplx acc = mkc(0.0, 0.0);
+  for (int m = threadIdx.x; m < A.n_occ; m += blockDim.x) {
+    const double f = -theta(A.eps[m] - omega);
+    if (f == 0.0) continue;
+    const double x = fabs(A.eps[m] - omega);
+    const cplx z2 = mkc(x * x - A.eta * A.eta, 2.0 * x * A.eta);
+    const double* P = A.poles + ((long)s * A.n_occ + m) * CDWAC_MLP_POLES * 2;
+    cplx T = mkc(0.0, 0.0);
+    for (int q = 0; q < CDWAC_MLP_POLES; ++q) {
+      const double Om = P[2 * q], r = P[2 * q + 1];
+      T = T - (r * 2.0 * Om) * (mkc(1.0, 0.0) / (mkc(Om * Om, 0.0) - z2));
+    }
+    acc = acc + f * T;
+  }
+  if (report && threadIdx.x == 0 && omega > A.eps[A.n_occ]) raise_status(status, DEV_ERR_BOUNDS);
+  return acc;
+}
+
 __device__ inline cplx block_sigma(const SigmaArgs& A, int s, double omega, cplx* red, unsigned* status,
                                    bool report = true) {
   cplx v = mkc(0.0, 0.0) - partial_I(A, s, omega);
   if (A.pa) v = v + partial_R_wac(A, s, omega, status, report);
+  else if (A.poles) v = v + partial_R_poles(A, s, omega, status, report);
   return block_sum(v, red);
 }
 
@@ -145,7 +168,7 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
   const double h = 1e-5;
   auto resig = [&](double w) { return block_sigma(A, s, w, red, status, false).x; };
   // the continuation covers residues of occupied orbitals only: an iterate above the LUMO ends the fixed point
-  const double upper = A.pa ? A.eps[A.n_occ] : INFINITY;
+  const double upper = (A.pa || A.poles) ? A.eps[A.n_occ] : INFINITY;
   auto zfac = [&](double e) {
     double d = (resig(e + h) - resig(e - h)) / (2.0 * h);
     return 1.0 / (1.0 - d);
@@ -238,6 +261,7 @@ SigmaArgs make_args(const cdwac_system* sys, const cdwac_params* prm, const doub
   A.pz2 = pade ? reinterpret_cast<const cplx*>(pade->z2) : nullptr;
   A.n_used = pade ? pade->n_used : nullptr;
   A.M_cap = pade ? pade->M : 0;
+  A.poles = nullptr;
   return A;
 }
 
@@ -267,6 +291,30 @@ cdwac_status launch_qp_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_
   SigmaArgs A = make_args(sys, prm, xi, wxi, W_imag, pade);
   qp_kernel<<<sys->n_states, SIG_THREADS, 0, st>>>(A, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters,
                                                      qp_status, ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+cdwac_status launch_sigma_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                                const double* wxi, const double* W_imag, const double* poles, const double* omega,
+                                int n_omega, double* sigma, cudaStream_t st) {
+  if (n_omega <= 0) return CDWAC_OK;
+  SigmaArgs A = make_args(sys, prm, xi, wxi, W_imag, nullptr);
+  A.poles = poles;
+  dim3 grid(n_omega, sys->n_states);
+  sigma_kernel<<<grid, SIG_THREADS, 0, st>>>(A, omega, n_omega, reinterpret_cast<cplx*>(sigma), ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+cdwac_status launch_qp_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                             const double* wxi, const double* W_imag, const double* poles, const double* shift,
+                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
+                             int* iters, int* qp_status, cudaStream_t st) {
+  SigmaArgs A = make_args(sys, prm, xi, wxi, W_imag, nullptr);
+  A.poles = poles;
+  qp_kernel<<<sys->n_states, SIG_THREADS, 0, st>>>(A, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters, qp_status,
+                                                     ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }
