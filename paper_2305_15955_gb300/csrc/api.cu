@@ -65,6 +65,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
     return CDWAC_ERR_UNSUPPORTED;
   }
   ctx->num_sms = p.multiProcessorCount;
+  if (const char* fl = getenv("CDWAC_FREQ_LANES")) ctx->freq_lanes = std::max(1, std::min(8, atoi(fl)));
   if (cudaStreamCreateWithFlags(&ctx->own_side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_bulk, cudaEventDisableTiming) != cudaSuccess) {
@@ -91,18 +92,25 @@ void cdwac_profile_enable(cdwac_ctx* ctx, int on) {
   if (ctx) ctx->prof = on < 0 ? 0 : (on > 2 ? 2 : on);
 }
 
-int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries) {
-  if (!ctx) return -1;
-  for (auto& r : ctx->prof_live) {
+static int drain_profile(cdwac_ctx* src, cdwac_ctx* dst) {
+  for (auto& r : src->prof_live) {
     if (cudaEventSynchronize(r.stop) != cudaSuccess) return -1;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, r.start, r.stop) != cudaSuccess) return -1;
-    ctx->prof_ms[r.cls] += ms;
-    ctx->prof_n[r.cls] += 1;
-    ctx->prof_pool.push_back(r.start);
-    ctx->prof_pool.push_back(r.stop);
+    dst->prof_ms[r.cls] += ms;
+    dst->prof_n[r.cls] += 1;
+    src->prof_pool.push_back(r.start);
+    src->prof_pool.push_back(r.stop);
   }
-  ctx->prof_live.clear();
+  src->prof_live.clear();
+  return 0;
+}
+
+int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries) {
+  if (!ctx) return -1;
+  if (drain_profile(ctx, ctx)) return -1;
+  for (auto* l : ctx->lanes)
+    if (drain_profile(l, ctx)) return -1;
   int k = 0;
   for (int c = 0; c < PROF_COUNT && k < max_entries; ++c) {
     if (ctx->prof_n[c] == 0) continue;
@@ -118,7 +126,12 @@ int cdwac_profile_read(cdwac_ctx* ctx, cdwac_profile_entry* out, int max_entries
   return k;
 }
 
-long long cdwac_launch_count(const cdwac_ctx* ctx) { return ctx ? ctx->launches : 0; }
+long long cdwac_launch_count(const cdwac_ctx* ctx) {
+  if (!ctx) return 0;
+  long long n = ctx->launches;
+  for (auto* l : ctx->lanes) n += l->launches;
+  return n;
+}
 
 void cdwac_destroy(cdwac_ctx* ctx) {
   if (!ctx) return;
@@ -237,6 +250,105 @@ static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols, int rhs_sets 
 
 extern "C" {
 
+// ---- frequency lanes: the per-frequency work of one call split over concurrent streams -------------------------
+// Each lane owns a context (own scratch, own LDL^T side stream) and takes frequencies k = l, l + L, ...; the
+// caller's stream forks to the lanes and joins them.  While one lane walks the sequential diagonal/panel steps of
+// its factorisation, the other's bulk trailing update keeps the FP64 units busy.
+
+static int freq_lanes(cdwac_ctx* ctx, int n_freq) {
+  if (ctx->is_lane) return 1;
+  int L = ctx->freq_lanes;
+  return std::max(1, std::min(L, n_freq));
+}
+
+static cdwac_status fork_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
+  cdwac_status rc = ensure_lanes(ctx, L);
+  if (rc) return rc;
+  CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, st));
+  for (int l = 0; l < L; ++l) {
+    ctx->lanes[l]->prof = ctx->prof;
+    ctx->lanes[l]->side_stream = ctx->lanes[l]->own_side;
+    CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->lane_streams[l], ctx->ev_fork, 0));
+  }
+  return CDWAC_OK;
+}
+
+static cdwac_status join_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
+  for (int l = 0; l < L; ++l) {
+    CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->lane_events[l], ctx->lane_streams[l]));
+    CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->lane_events[l], 0));
+  }
+  return CDWAC_OK;
+}
+
+struct ImagBufs {
+  FactorScratch<double> f;
+  double* pidiag;
+  double* V;
+  void* tc_lane;
+  float* negpi32;
+  void* ws32;
+};
+
+// FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: FP32 solves of the
+// same form on the tensor-core Pi (wsolve32).
+static size_t imag_lane_bytes(const cdwac_system* sys, bool mixed) {
+  const int n = sys->n_aux, nb = sys->n_basis, cols = sys->n_states * nb;
+  const long n_ov = (long)sys->n_occ * (nb - sys->n_occ);
+  size_t b = factor_scratch_bytes<double>(n, cols, mixed ? 0 : 2) + 4096;
+  if (!mixed) b += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
+  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) + 1024;
+  return b;
+}
+
+static ImagBufs carve_imag(Arena& ar, const cdwac_system* sys, bool mixed) {
+  const int n = sys->n_aux, nb = sys->n_basis, cols = sys->n_states * nb;
+  const long n_ov = (long)sys->n_occ * (nb - sys->n_occ);
+  ImagBufs b;
+  b.f = carve_factor<double>(ar, n, cols, mixed ? 0 : 2);
+  b.pidiag = mixed ? nullptr : ar.take<double>(n);
+  b.V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
+  b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov)) : nullptr;
+  b.negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
+  b.ws32 = mixed ? ar.take<char>(wsolve32_scratch_bytes(n, cols)) : nullptr;
+  return b;
+}
+
+static cdwac_status imag_freqs(cdwac_ctx* lc, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                               double* W_imag, const double* D, const void* tc_shared, const ImagBufs& b, int k0,
+                               int kstep, cudaStream_t st) {
+  const int n = sys->n_aux, nb = sys->n_basis;
+  const long n_ov = (long)sys->n_occ * (nb - sys->n_occ);
+  const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  cdwac_status rc;
+  for (int k = k0; k < prm->n_imag; k += kstep) {
+    if (mixed) {
+      rc = tc_pi_imag(lc, tc_shared, b.tc_lane, sys->O_ia, sys->O_dtype, D, n, n_ov, xi + k, b.f.A, b.negpi32, st);
+    } else {
+      ProfScope ps(lc, PROF_PI_SIMT, st);
+      rc = launch_pi_imag_fp64(lc, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, b.f.A, b.pidiag, st);
+    }
+    if (rc) return rc;
+    {
+      ProfScope ps(lc, PROF_LDLT, st);
+      if ((rc = ldlt_factor<double>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st))) return rc;
+    }
+    ProfScope ps(lc, PROF_QUADFORM, st);
+    if (mixed) {
+      rc = wsolve32(lc, b.f.A, b.f.dinv, b.f.linv, b.negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
+                    sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, b.ws32, st);
+    } else {
+      if ((rc = launch_pi_times_o(lc, b.f.A, b.pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
+                                  b.V, st)))
+        return rc;
+      rc = ldlt_quadform_pi(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, b.V, (long)n * nb, nb,
+                            sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, b.f.ywork, st);
+    }
+    if (rc) return rc;
+  }
+  return CDWAC_OK;
+}
+
 cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
                                 double* wxi, double* W_imag, void* stream) {
   cdwac_status rc = check_system(ctx, sys, prm);
@@ -246,23 +358,20 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   cudaStream_t st = (cudaStream_t)stream;
   const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
   const long n_ov = (long)n_occ * n_virt;
-  const int cols = sys->n_states * nb;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
-  // FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: |L^-1 o|^2/d - |o|^2
-  size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<double>(n, cols, mixed ? 0 : 2) + 4096;
-  if (!mixed) bytes += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
-  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) + 512;
+  const int L = freq_lanes(ctx, prm->n_imag);
+  size_t bytes = n_ov * sizeof(double) + (mixed ? tc_pi_shared_bytes(n, n_ov) : 0) + 1024;
+  if (L == 1) bytes += imag_lane_bytes(sys, mixed);
   rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
+  if (L > 1) {
+    if ((rc = ensure_lanes(ctx, L))) return rc;
+    for (int l = 0; l < L; ++l)
+      if ((rc = ensure_scratch(ctx->lanes[l], imag_lane_bytes(sys, mixed)))) return set_error(ctx, rc, "lane scratch");
+  }
   Arena ar(ctx->scratch);
   double* D = ar.take<double>(n_ov);
-  FactorScratch<double> f = carve_factor<double>(ar, n, cols, mixed ? 0 : 2);
-  double* pidiag = mixed ? nullptr : ar.take<double>(n);
-  double* V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
-  void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
-  float* negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
-  void* ws32 = mixed ? ar.take<char>(wsolve32_scratch_bytes(n, cols)) : nullptr;
-
+  void* tc_shared = mixed ? ar.take<char>(tc_pi_shared_bytes(n, n_ov)) : nullptr;
   {
     ProfScope ps(ctx, PROF_GRID, st);
     if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
@@ -270,31 +379,72 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   }
   if (mixed) {
     ProfScope ps(ctx, PROF_PI_PREP, st);
-    if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+    if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tc_shared, st))) return rc;
   }
-  for (int k = 0; k < prm->n_imag; ++k) {
+  if (L == 1) {
+    ImagBufs b = carve_imag(ar, sys, mixed);
+    return imag_freqs(ctx, sys, prm, xi, W_imag, D, tc_shared, b, 0, 1, st);
+  }
+  if ((rc = fork_lanes(ctx, L, st))) return rc;
+  for (int l = 0; l < L; ++l) {
+    Arena al(ctx->lanes[l]->scratch);
+    ImagBufs b = carve_imag(al, sys, mixed);
+    rc = imag_freqs(ctx->lanes[l], sys, prm, xi, W_imag, D, tc_shared, b, l, L, ctx->lane_streams[l]);
+    if (rc) return set_error(ctx, rc, "lane %d: %s", l, ctx->lanes[l]->last_error.c_str());
+  }
+  return join_lanes(ctx, L, st);
+}
+
+struct RealBufs {
+  FactorScratch<cplx> f;
+  void* tc_lane;
+  void* wsc;
+};
+
+static size_t real_lane_bytes(const cdwac_system* sys, bool mixed) {
+  const int n = sys->n_aux, ns = sys->n_states, n_occ = sys->n_occ;
+  const long n_ov = (long)n_occ * (sys->n_basis - n_occ);
+  size_t b = factor_scratch_bytes<cplx>(n, ns * n_occ) + 2048;
+  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ) + 512;
+  return b;
+}
+
+static RealBufs carve_real(Arena& ar, const cdwac_system* sys, bool mixed) {
+  const int n = sys->n_aux, ns = sys->n_states, n_occ = sys->n_occ;
+  const long n_ov = (long)n_occ * (sys->n_basis - n_occ);
+  RealBufs b;
+  b.f = carve_factor<cplx>(ar, n, ns * n_occ);
+  b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov)) : nullptr;
+  b.wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns * n_occ)) : nullptr;
+  return b;
+}
+
+static cdwac_status real_points(cdwac_ctx* lc, const cdwac_system* sys, const cdwac_params* prm, const cplx* zr,
+                                cplx* Wr, const double* D, const void* tc_shared, const RealBufs& b, int j0, int jstep,
+                                cudaStream_t st) {
+  const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, ns = sys->n_states, nr = prm->n_real;
+  const long n_ov = (long)n_occ * (nb - n_occ);
+  const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  cdwac_status rc;
+  for (int j = j0; j < nr; j += jstep) {
     if (mixed) {
-      rc = tc_pi_imag(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, xi + k, f.A, negpi32, st);
+      rc = tc_pi_complex(lc, tc_shared, b.tc_lane, sys->O_ia, sys->O_dtype, D, n, n_ov, zr + j, b.f.A, st);
     } else {
-      ProfScope ps(ctx, PROF_PI_SIMT, st);
-      rc = launch_pi_imag_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, xi + k, f.A, pidiag, st);
+      ProfScope ps(lc, PROF_PI_SIMT, st);
+      rc = launch_pi_complex_fp64(lc, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zr + j, b.f.A, st);
     }
     if (rc) return rc;
     {
-      ProfScope ps(ctx, PROF_LDLT, st);
-      if ((rc = ldlt_factor<double>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      ProfScope ps(lc, PROF_LDLT, st);
+      if ((rc = ldlt_factor<cplx>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st))) return rc;
     }
-    ProfScope ps(ctx, PROF_QUADFORM, st);
-    if (mixed) {
-      rc = wsolve32(ctx, f.A, f.dinv, f.linv, negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
-                    W_imag + (long)k * nb, (long)prm->n_imag * nb, ws32, st);
-    } else {
-      if ((rc = launch_pi_times_o(ctx, f.A, pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
-                                  V, st)))
-        return rc;
-      rc = ldlt_quadform_pi(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, V, (long)n * nb, nb,
-                            sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, f.ywork, st);
-    }
+    ProfScope ps(lc, PROF_QUADFORM, st);
+    if (mixed)
+      rc = wsolve_c32(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
+                      Wr + (long)j * n_occ, (long)nr * n_occ, b.wsc, st);
+    else
+      rc = ldlt_quadform<cplx>(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
+                               Wr + (long)j * n_occ, (long)nr * n_occ, b.f.ywork, st);
     if (rc) return rc;
   }
   return CDWAC_OK;
@@ -316,47 +466,43 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
   const long n_ov = (long)n_occ * n_virt;
   const int nr = prm->n_real, ns = sys->n_states;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
+  const int L = nr > 0 ? freq_lanes(ctx, nr) : 1;
   size_t bytes = n_ov * sizeof(double) + 2 * sizeof(cplx) * (size_t)ns * nr * (n_occ + 1) + 4096;
-  if (nr > 0) bytes += factor_scratch_bytes<cplx>(n, ns * n_occ);
-  if (mixed && nr > 0) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ);
+  if (mixed && nr > 0) bytes += tc_pi_shared_bytes(n, n_ov);
+  if (nr > 0 && L == 1) bytes += real_lane_bytes(sys, mixed);
   rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
+  if (nr > 0 && L > 1) {
+    if ((rc = ensure_lanes(ctx, L))) return rc;
+    for (int l = 0; l < L; ++l)
+      if ((rc = ensure_scratch(ctx->lanes[l], real_lane_bytes(sys, mixed)))) return set_error(ctx, rc, "lane scratch");
+  }
   Arena ar(ctx->scratch);
   double* D = ar.take<double>(n_ov);
   cplx* zr = z_real ? reinterpret_cast<cplx*>(z_real) : ar.take<cplx>((size_t)ns * nr + 1);
   cplx* Wr = W_real ? reinterpret_cast<cplx*>(W_real) : ar.take<cplx>((size_t)ns * nr * n_occ + 1);
   if (nr > 0) {
-    FactorScratch<cplx> f = carve_factor<cplx>(ar, n, ns * n_occ);
-    void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
-    void* wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns * n_occ)) : nullptr;
+    void* tc_shared = mixed ? ar.take<char>(tc_pi_shared_bytes(n, n_ov)) : nullptr;
     if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
     if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, nr, prm->eta_ref, prm->real_margin,
                                       reinterpret_cast<double*>(zr), st)))
       return rc;
     if (mixed) {
       ProfScope ps(ctx, PROF_PI_PREP, st);
-      if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
+      if ((rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tc_shared, st))) return rc;
     }
-    for (int j = 0; j < nr; ++j) {
-      if (mixed) {
-        rc = tc_pi_complex(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, zr + j, f.A, st);
-      } else {
-        ProfScope ps(ctx, PROF_PI_SIMT, st);
-        rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zr + j, f.A, st);
+    if (L == 1) {
+      RealBufs b = carve_real(ar, sys, mixed);
+      if ((rc = real_points(ctx, sys, prm, zr, Wr, D, tc_shared, b, 0, 1, st))) return rc;
+    } else {
+      if ((rc = fork_lanes(ctx, L, st))) return rc;
+      for (int l = 0; l < L; ++l) {
+        Arena al(ctx->lanes[l]->scratch);
+        RealBufs b = carve_real(al, sys, mixed);
+        rc = real_points(ctx->lanes[l], sys, prm, zr, Wr, D, tc_shared, b, l, L, ctx->lane_streams[l]);
+        if (rc) return set_error(ctx, rc, "lane %d: %s", l, ctx->lanes[l]->last_error.c_str());
       }
-      if (rc) return rc;
-      {
-        ProfScope ps(ctx, PROF_LDLT, st);
-        if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
-      }
-      ProfScope ps(ctx, PROF_QUADFORM, st);
-      if (mixed)
-        rc = wsolve_c32(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
-                        Wr + (long)j * n_occ, (long)nr * n_occ, wsc, st);
-      else
-        rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
-                                 Wr + (long)j * n_occ, (long)nr * n_occ, f.ywork, st);
-      if (rc) return rc;
+      if ((rc = join_lanes(ctx, L, st))) return rc;
     }
   }
   ProfScope ps(ctx, PROF_THIELE, st);
@@ -408,7 +554,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
       set_z_kernel<<<1, 1, 0, st>>>(zdev, fabs(eps[m] - w), prm->eta);
       CDWAC_LAUNCH_CHECK(ctx);
       if (mixed)
-        rc = tc_pi_complex(ctx, tcs, sys->O_ia, sys->O_dtype, D, n, n_ov, zdev, f.A, st);
+        rc = tc_pi_complex(ctx, tcs, tc_pi_lane_part(tcs, n, n_ov), sys->O_ia, sys->O_dtype, D, n, n_ov, zdev, f.A, st);
       else
         rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zdev, f.A, st);
       if (rc) return rc;

@@ -44,9 +44,12 @@ cdwac_status make_lane(cdwac_ctx* parent, cdwac_ctx** out) {
     return set_error(parent, CDWAC_ERR_CUDA, "lane creation failed");
   }
   l->side_stream = l->own_side;
+  l->freq_lanes = 1;
   *out = l;
   return CDWAC_OK;
 }
+
+}  // namespace
 
 cdwac_status ensure_lanes(cdwac_ctx* ctx, int n) {
   if (!ctx->ev_fork) CDWAC_CUDA_TRY(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
@@ -64,6 +67,8 @@ cdwac_status ensure_lanes(cdwac_ctx* ctx, int n) {
   }
   return CDWAC_OK;
 }
+
+namespace {
 
 cdwac_status run_item(cdwac_ctx* lane, const cdwac_batch_item& it, const cdwac_params* prm, double tol, int max_iter,
                       cudaStream_t s) {

@@ -62,6 +62,7 @@ struct cdwac_ctx {
   cudaEvent_t ev_panel = nullptr, ev_bulk = nullptr;
   // batched launch: lane contexts (own scratch and streams, shared status word), fork/join events, graph cache
   bool is_lane = false;
+  int freq_lanes = 2;                   // concurrent frequency chains in the W builds (lanes never nest)
   std::vector<cdwac_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_events;
@@ -117,6 +118,8 @@ struct Arena {
 };
 
 cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes);
+// batch.cu: lane contexts (own scratch, own side stream, the parent's status word) and their streams/events
+cdwac_status ensure_lanes(cdwac_ctx* ctx, int n);
 cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...);
 
 #define CDWAC_CUDA_TRY(ctx, expr)                                                                 \

@@ -388,19 +388,21 @@ struct Scratch {
 
 long kpad_of(long n_ov) { return ((n_ov + BK - 1) / BK) * BK; }
 
-Scratch carve(void* base, int n, long n_ov) {
+// Shared region: the BF16 planes of O^{ia} (read by every lane).  Lane region: the weighted planes and weights.
+Scratch carve(const void* shared, void* lane, int n, long n_ov) {
   Scratch s;
   const long kp = kpad_of(n_ov);
   const size_t plane = (size_t)n * kp;
-  Arena ar(base);
-  s.bh = ar.take<__nv_bfloat16>(plane);
-  s.bl = ar.take<__nv_bfloat16>(plane);
-  s.s0h = ar.take<__nv_bfloat16>(plane);
-  s.s0l = ar.take<__nv_bfloat16>(plane);
-  s.s1h = ar.take<__nv_bfloat16>(plane);
-  s.s1l = ar.take<__nv_bfloat16>(plane);
-  s.w0 = ar.take<float>(kp);
-  s.w1 = ar.take<float>(kp);
+  Arena as(const_cast<void*>(shared));
+  s.bh = as.take<__nv_bfloat16>(plane);
+  s.bl = as.take<__nv_bfloat16>(plane);
+  Arena al(lane);
+  s.s0h = al.take<__nv_bfloat16>(plane);
+  s.s0l = al.take<__nv_bfloat16>(plane);
+  s.s1h = al.take<__nv_bfloat16>(plane);
+  s.s1l = al.take<__nv_bfloat16>(plane);
+  s.w0 = al.take<float>(kp);
+  s.w1 = al.take<float>(kp);
   s.kpad = kp;
   return s;
 }
@@ -454,14 +456,27 @@ cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, float* n
 
 }  // namespace
 
-size_t tc_pi_scratch_bytes(int n_aux, long n_ov) {
+size_t tc_pi_shared_bytes(int n_aux, long n_ov) {
   const long kp = kpad_of(n_ov);
-  return 256 + 6 * ((size_t)n_aux * kp * 2 + 256) + 2 * ((size_t)kp * 4 + 256) + 1024;
+  return 2 * ((size_t)n_aux * kp * 2 + 256) + 512;
+}
+
+size_t tc_pi_lane_bytes(int n_aux, long n_ov) {
+  const long kp = kpad_of(n_ov);
+  return 4 * ((size_t)n_aux * kp * 2 + 256) + 2 * ((size_t)kp * 4 + 256) + 512;
+}
+
+size_t tc_pi_scratch_bytes(int n_aux, long n_ov) {
+  return tc_pi_shared_bytes(n_aux, n_ov) + tc_pi_lane_bytes(n_aux, n_ov) + 256;
+}
+
+void* tc_pi_lane_part(void* scratch, int n_aux, long n_ov) {
+  return static_cast<char*>(scratch) + ((tc_pi_shared_bytes(n_aux, n_ov) + 255) & ~size_t(255));
 }
 
 cdwac_status tc_pi_prepare(cdwac_ctx* ctx, const void* O_ia, int dtype, int n_aux, long n_ov, void* scratch,
                            cudaStream_t st) {
-  Scratch s = carve(scratch, n_aux, n_ov);
+  Scratch s = carve(scratch, nullptr, n_aux, n_ov);
   const int blocks = elementwise_blocks(ctx, (long)n_aux * (s.kpad / 8));
   if (dtype == CDWAC_F64)
     split_kernel<double><<<blocks, 256, 0, st>>>((const double*)O_ia, n_aux, n_ov, s.kpad, s.bh, s.bl);
@@ -496,9 +511,9 @@ static cdwac_status scale(cdwac_ctx* ctx, const Scratch& s, const void* O_ia, in
   return CDWAC_OK;
 }
 
-cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
-                        long n_ov, const double* xi_dev, double* A, float* negpi32, cudaStream_t st) {
-  Scratch s = carve(scratch, n_aux, n_ov);
+cdwac_status tc_pi_imag(cdwac_ctx* ctx, const void* shared, void* lane, const void* O_ia, int dtype, const double* D,
+                        int n_aux, long n_ov, const double* xi_dev, double* A, float* negpi32, cudaStream_t st) {
+  Scratch s = carve(shared, lane, n_aux, n_ov);
   cdwac_status rc;
   {
     ProfScope ps(ctx, PROF_PI_PREP, st);
@@ -509,9 +524,9 @@ cdwac_status tc_pi_imag(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dty
   return run_syrk<1>(ctx, s, n_aux, A, negpi32, st);
 }
 
-cdwac_status tc_pi_complex(cdwac_ctx* ctx, void* scratch, const void* O_ia, int dtype, const double* D, int n_aux,
-                           long n_ov, const cplx* z_dev, cplx* A, cudaStream_t st) {
-  Scratch s = carve(scratch, n_aux, n_ov);
+cdwac_status tc_pi_complex(cdwac_ctx* ctx, const void* shared, void* lane, const void* O_ia, int dtype,
+                           const double* D, int n_aux, long n_ov, const cplx* z_dev, cplx* A, cudaStream_t st) {
+  Scratch s = carve(shared, lane, n_aux, n_ov);
   cdwac_status rc;
   {
     ProfScope ps(ctx, PROF_PI_PREP, st);
