@@ -53,8 +53,10 @@ typedef enum { CDWAC_F64 = 0, CDWAC_F32 = 1 } cdwac_dtype;
 
 /* Arithmetic of the W build.  FP64: every contraction in FP64 (parity path).  MIXED: Pi and the near-real
  * Pi(z) as split-BF16 (hi/lo, three products) tcgen05 tensor-core contractions with FP32 accumulation; the
- * Cholesky / LDL^T, the W projection, the Thiele fit and the residue sum stay FP64; the I_n quadrature terms
- * are FP32 with FP64 partial sums. */
+ * Cholesky / LDL^T stays FP64-accurate (diagonal blocks and panels on the FP64 units, trailing updates as exact
+ * BF16 digit products on the tensor cores, CDWAC_LDLT_EMULATED below); the W solves run in FP32 on the FP64
+ * factor; the Thiele fit and the residue sum stay FP64; the I_n quadrature terms are FP32 with FP64 partial
+ * sums. */
 typedef enum { CDWAC_PREC_FP64 = 0, CDWAC_PREC_MIXED = 1 } cdwac_precision;
 
 typedef struct cdwac_ctx cdwac_ctx;
@@ -186,6 +188,25 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
+
+/* ---- the factorisation step on its own -------------------------------------------------------------- */
+
+/* Trailing-update arithmetic of the LDL^T factorisation. */
+typedef enum {
+  CDWAC_LDLT_FP64 = 0,      /* every update on the FP64 FMA units */
+  CDWAC_LDLT_EMULATED = 1   /* rank-64 trailing updates on the tcgen05 tensor cores from exact BF16 digits of
+                               the FP64 operands (8 digits of 7 bits per row, 36 digit products, exact FP32
+                               level sums recombined in FP64): FP64-equivalent accuracy */
+} cdwac_ldlt_method;
+
+/* Square-root-free Cholesky factorisation A = L D L^T of the symmetric matrix I - Pi of Eq. bigLambda (real
+ * symmetric positive definite on the imaginary axis, complex symmetric without pivoting near the real axis).
+ *   A  [n][n] device, row-major, FP64 (is_complex = 0) or interleaved complex FP64 (is_complex = 1).  Only the
+ *      lower triangle is read; on return it holds the unit-lower L below the diagonal and D on the diagonal.
+ *      The strict upper triangle is not touched.  The caller owns A; the context owns the scratch.
+ * A non-positive real pivot (CDWAC_ERR_NOT_SPD) or a vanishing complex pivot (CDWAC_ERR_SINGULAR) goes to the
+ * device status word and the factorisation continues with a unit pivot. */
+cdwac_status cdwac_ldlt_factor(cdwac_ctx* ctx, void* A, int n, int is_complex, int method, void* stream);
 
 /* ---- batched launch ------------------------------------------------------------------------------------ */
 

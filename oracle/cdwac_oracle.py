@@ -128,6 +128,23 @@ def screened_lambda(Pi):
     return scipy.linalg.lu_solve(lu, Pi)
 
 
+def ldlt_nopivot(A):
+    """Square-root-free Cholesky A = L D L^T without pivoting of the symmetric matrix I - Pi (Eq. bigLambda):
+    real symmetric positive definite on the imaginary axis, complex symmetric (transpose, not conjugate) near the
+    real axis.  Column by column (Crout order):
+        d_j  = A_jj - sum_{k<j} L_jk^2 d_k,
+        L_ij = (A_ij - sum_{k<j} L_ik d_k L_jk) / d_j,   i > j.
+    Returns (L unit lower triangular, d).  Reads only the lower triangle of A."""
+    A = np.asarray(A)
+    n = A.shape[0]
+    L = np.eye(n, dtype=A.dtype)
+    d = np.zeros(n, dtype=A.dtype)
+    for j in range(n):
+        d[j] = A[j, j] - np.sum(L[j, :j] ** 2 * d[:j])
+        L[j + 1:, j] = (A[j + 1:, j] - (L[j + 1:, :j] * d[:j]) @ L[j, :j]) / d[j]
+    return L, d
+
+
 def w_elements(On_s, Lam, m_idx=None):
     """W^c_nm = sum_PQ O^{nm}_P Lambda_PQ O^{mn}_Q, Eq. wriv, for one state n and orbitals m.
 

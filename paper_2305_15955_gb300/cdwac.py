@@ -23,6 +23,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOT_SPD", "ERR_SINGULAR", "ERR
                 "ERR_QP_NOT_CONVERGED", "ERR_TIMEOUT", "ERR_OOM", "ERR_UNSUPPORTED"]
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+LDLT_FP64, LDLT_EMULATED = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
@@ -108,6 +109,7 @@ def load():
     lib.cdwac_launch_count.argtypes = [P]
     lib.cdwac_launch_count.restype = ctypes.c_longlong
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
+    lib.cdwac_ldlt_factor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     lib.cdwac_mlp_features.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                        ctypes.c_int, P, P, P, P, P]
     lib.cdwac_mlp_loss_grad.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
@@ -317,6 +319,19 @@ class Context:
 
     def _dev(self):
         return torch.device("cuda", self.device)
+
+    def ldlt_factor(self, A, method: int = LDLT_FP64, sync: bool = True):
+        """cdwac_ldlt_factor in place on a square float64 or complex128 CUDA tensor (row-major, contiguous): the
+        lower triangle becomes the unit-lower L (below the diagonal) and D (on it)."""
+        if A.dim() != 2 or A.shape[0] != A.shape[1] or not A.is_contiguous():
+            raise ValueError("A must be a contiguous square matrix")
+        if A.dtype not in (torch.float64, torch.complex128):
+            raise ValueError("A must be float64 or complex128")
+        self._check(self.lib.cdwac_ldlt_factor(self.h, _ptr(A), A.shape[0], int(A.dtype == torch.complex128),
+                                               int(method), self._stream()))
+        if sync:
+            self.sync_status()
+        return A
 
     def build_W_imag(self, system: System, params: Params, sync: bool = True):
         dev = self._dev()

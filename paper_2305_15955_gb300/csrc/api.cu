@@ -43,6 +43,20 @@ cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes) {
   return CDWAC_OK;
 }
 
+bool create_factor_streams(cdwac_ctx* ctx) {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return false;
+  if (cudaStreamCreateWithPriority(&ctx->own_side, cudaStreamNonBlocking, least) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&ctx->crit_stream, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_bulk, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_crit_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_crit_out, cudaEventDisableTiming) != cudaSuccess)
+    return false;
+  ctx->side_stream = ctx->own_side;
+  return true;
+}
+
 extern "C" {
 
 cdwac_status cdwac_create(cdwac_ctx** out, int device) {
@@ -65,14 +79,11 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
     return CDWAC_ERR_UNSUPPORTED;
   }
   ctx->num_sms = p.multiProcessorCount;
-  if (const char* fl = getenv("CDWAC_FREQ_LANES")) ctx->freq_lanes = std::max(1, std::min(8, atoi(fl)));
-  if (cudaStreamCreateWithFlags(&ctx->own_side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_bulk, cudaEventDisableTiming) != cudaSuccess) {
-    delete ctx;
+  if (const char* fl = getenv("CDWAC_FREQ_LANES")) ctx->freq_lanes = std::max(1, std::min(16, atoi(fl)));
+  if (!create_factor_streams(ctx)) {
+    cdwac_destroy(ctx);
     return CDWAC_ERR_CUDA;
   }
-  ctx->side_stream = ctx->own_side;
   if (cudaMalloc(&ctx->d_status, sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(ctx->d_status, 0, sizeof(unsigned)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess) {
@@ -148,7 +159,10 @@ void cdwac_destroy(cdwac_ctx* ctx) {
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   if (ctx->ev_panel) cudaEventDestroy(ctx->ev_panel);
   if (ctx->ev_bulk) cudaEventDestroy(ctx->ev_bulk);
+  if (ctx->ev_crit_in) cudaEventDestroy(ctx->ev_crit_in);
+  if (ctx->ev_crit_out) cudaEventDestroy(ctx->ev_crit_out);
   if (ctx->own_side) cudaStreamDestroy(ctx->own_side);
+  if (ctx->crit_stream) cudaStreamDestroy(ctx->crit_stream);
   if (ctx->scratch) cudaFree(ctx->scratch);
   if (!ctx->is_lane) {
     if (ctx->d_status) cudaFree(ctx->d_status);
@@ -250,15 +264,56 @@ static FactorScratch<T> carve_factor(Arena& ar, int n, int n_cols, int rhs_sets 
 
 extern "C" {
 
+cdwac_status cdwac_ldlt_factor(cdwac_ctx* ctx, void* A, int n, int is_complex, int method, void* stream) {
+  if (!ctx) return CDWAC_ERR_ARG;
+  if (!A || n <= 0) return set_error(ctx, CDWAC_ERR_ARG, "null matrix or n <= 0");
+  if (method != CDWAC_LDLT_FP64 && method != CDWAC_LDLT_EMULATED)
+    return set_error(ctx, CDWAC_ERR_ARG, "unknown factorisation method %d", method);
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool cx = is_complex != 0;
+  const bool emu = method == CDWAC_LDLT_EMULATED;
+  const size_t el = cx ? sizeof(cplx) : sizeof(double);
+  size_t bytes = ldlt_scratch_elems<double>(n) * el + 1024;
+  if (emu) bytes += ldlt_tc_scratch_bytes(n, cx);
+  cdwac_status rc = ensure_scratch(ctx, bytes);
+  if (rc) return rc;
+  Arena ar(ctx->scratch);
+  const int nblk = (n + 63) / 64;
+  ProfScope ps(ctx, PROF_LDLT, st);
+  if (cx) {
+    cplx* dinv = ar.take<cplx>(n);
+    cplx* linv = ar.take<cplx>((size_t)nblk * 64 * 64);
+    cplx* wpanel = ar.take<cplx>(2 * (size_t)(nblk + 1) * 64 * 64);
+    void* oz = emu ? ar.take<char>(ldlt_tc_scratch_bytes(n, true)) : nullptr;
+    return ldlt_factor<cplx>(ctx, static_cast<cplx*>(A), n, dinv, linv, wpanel, st, oz);
+  }
+  double* dinv = ar.take<double>(n);
+  double* linv = ar.take<double>((size_t)nblk * 64 * 64);
+  double* wpanel = ar.take<double>(2 * (size_t)(nblk + 1) * 64 * 64);
+  void* oz = emu ? ar.take<char>(ldlt_tc_scratch_bytes(n, false)) : nullptr;
+  return ldlt_factor<double>(ctx, static_cast<double*>(A), n, dinv, linv, wpanel, st, oz);
+}
+
 // ---- frequency lanes: the per-frequency work of one call split over concurrent streams -------------------------
 // Each lane owns a context (own scratch, own LDL^T side stream) and takes frequencies k = l, l + L, ...; the
 // caller's stream forks to the lanes and joins them.  While one lane walks the sequential diagonal/panel steps of
 // its factorisation, the other's bulk trailing update keeps the FP64 units busy.
 
-static int freq_lanes(cdwac_ctx* ctx, int n_freq) {
+// Lanes for n_freq frequencies whose per-lane scratch is lane_bytes: at most ctx->freq_lanes, and no more than
+// half of the device memory that is free (plus what the lanes already hold) can carry.
+static int freq_lanes(cdwac_ctx* ctx, int n_freq, size_t lane_bytes) {
   if (ctx->is_lane) return 1;
-  int L = ctx->freq_lanes;
-  return std::max(1, std::min(L, n_freq));
+  int L = std::max(1, std::min(ctx->freq_lanes, n_freq));
+  size_t free_b = 0, total_b = 0;
+  if (L > 1 && cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+    size_t held = 0;
+    for (auto* l : ctx->lanes) held += l->scratch_bytes;
+    const size_t budget = (free_b + held) / 2;
+    const int fit = (int)std::min<size_t>(budget / std::max<size_t>(lane_bytes, 1), 64);
+    L = std::max(1, std::min(L, fit));
+  }
+  return L;
 }
 
 static cdwac_status fork_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
@@ -283,6 +338,7 @@ static cdwac_status join_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
 
 struct ImagBufs {
   FactorScratch<double> f;
+  void* oz;
   double* pidiag;
   double* V;
   void* tc_lane;
@@ -297,7 +353,9 @@ static size_t imag_lane_bytes(const cdwac_system* sys, bool mixed) {
   const long n_ov = (long)sys->n_occ * (nb - sys->n_occ);
   size_t b = factor_scratch_bytes<double>(n, cols, mixed ? 0 : 2) + 4096;
   if (!mixed) b += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
-  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) + 1024;
+  if (mixed)
+    b += tc_pi_lane_bytes(n, n_ov, 1) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) +
+         ldlt_tc_scratch_bytes(n, false) + 1280;
   return b;
 }
 
@@ -308,9 +366,10 @@ static ImagBufs carve_imag(Arena& ar, const cdwac_system* sys, bool mixed) {
   b.f = carve_factor<double>(ar, n, cols, mixed ? 0 : 2);
   b.pidiag = mixed ? nullptr : ar.take<double>(n);
   b.V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
-  b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov)) : nullptr;
+  b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov, 1)) : nullptr;
   b.negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
   b.ws32 = mixed ? ar.take<char>(wsolve32_scratch_bytes(n, cols)) : nullptr;
+  b.oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, false)) : nullptr;
   return b;
 }
 
@@ -331,7 +390,7 @@ static cdwac_status imag_freqs(cdwac_ctx* lc, const cdwac_system* sys, const cdw
     if (rc) return rc;
     {
       ProfScope ps(lc, PROF_LDLT, st);
-      if ((rc = ldlt_factor<double>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st))) return rc;
+      if ((rc = ldlt_factor<double>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st, b.oz))) return rc;
     }
     ProfScope ps(lc, PROF_QUADFORM, st);
     if (mixed) {
@@ -359,7 +418,7 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
   const long n_ov = (long)n_occ * n_virt;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
-  const int L = freq_lanes(ctx, prm->n_imag);
+  const int L = freq_lanes(ctx, prm->n_imag, imag_lane_bytes(sys, mixed));
   size_t bytes = n_ov * sizeof(double) + (mixed ? tc_pi_shared_bytes(n, n_ov) : 0) + 1024;
   if (L == 1) bytes += imag_lane_bytes(sys, mixed);
   rc = ensure_scratch(ctx, bytes);
@@ -397,6 +456,7 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
 
 struct RealBufs {
   FactorScratch<cplx> f;
+  void* oz;
   void* tc_lane;
   void* wsc;
 };
@@ -405,7 +465,7 @@ static size_t real_lane_bytes(const cdwac_system* sys, bool mixed) {
   const int n = sys->n_aux, ns = sys->n_states, n_occ = sys->n_occ;
   const long n_ov = (long)n_occ * (sys->n_basis - n_occ);
   size_t b = factor_scratch_bytes<cplx>(n, ns * n_occ) + 2048;
-  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ) + 512;
+  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ) + ldlt_tc_scratch_bytes(n, true) + 768;
   return b;
 }
 
@@ -416,6 +476,7 @@ static RealBufs carve_real(Arena& ar, const cdwac_system* sys, bool mixed) {
   b.f = carve_factor<cplx>(ar, n, ns * n_occ);
   b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov)) : nullptr;
   b.wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns * n_occ)) : nullptr;
+  b.oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, true)) : nullptr;
   return b;
 }
 
@@ -436,7 +497,7 @@ static cdwac_status real_points(cdwac_ctx* lc, const cdwac_system* sys, const cd
     if (rc) return rc;
     {
       ProfScope ps(lc, PROF_LDLT, st);
-      if ((rc = ldlt_factor<cplx>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st))) return rc;
+      if ((rc = ldlt_factor<cplx>(lc, b.f.A, n, b.f.dinv, b.f.linv, b.f.wpanel, st, b.oz))) return rc;
     }
     ProfScope ps(lc, PROF_QUADFORM, st);
     if (mixed)
@@ -466,7 +527,7 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
   const long n_ov = (long)n_occ * n_virt;
   const int nr = prm->n_real, ns = sys->n_states;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
-  const int L = nr > 0 ? freq_lanes(ctx, nr) : 1;
+  const int L = nr > 0 ? freq_lanes(ctx, nr, real_lane_bytes(sys, mixed)) : 1;
   size_t bytes = n_ov * sizeof(double) + 2 * sizeof(cplx) * (size_t)ns * nr * (n_occ + 1) + 4096;
   if (mixed && nr > 0) bytes += tc_pi_shared_bytes(n, n_ov);
   if (nr > 0 && L == 1) bytes += real_lane_bytes(sys, mixed);
@@ -532,7 +593,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   const int ns = sys->n_states;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
   size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<cplx>(n, ns) + sizeof(cplx) * (ns + 2) + 2048;
-  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns);
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns) + ldlt_tc_scratch_bytes(n, true) + 512;
   cdwac_status rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
@@ -542,6 +603,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   cplx* Wv = ar.take<cplx>(ns);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
   void* wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns)) : nullptr;
+  void* oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, true)) : nullptr;
   if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
   if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
   for (size_t j = 0; j < omega.size(); ++j) {
@@ -558,7 +620,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
       else
         rc = launch_pi_complex_fp64(ctx, sys->O_ia, sys->O_dtype, D, n, (int)n_ov, zdev, f.A, st);
       if (rc) return rc;
-      if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st))) return rc;
+      if ((rc = ldlt_factor<cplx>(ctx, f.A, n, f.dinv, f.linv, f.wpanel, st, oz))) return rc;
       // column m of every state's O_n
       const void* Om = sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + m)
                                                  : (const void*)((const float*)sys->O_n + m);

@@ -37,13 +37,10 @@ cdwac_status make_lane(cdwac_ctx* parent, cdwac_ctx** out) {
   l->num_sms = parent->num_sms;
   l->d_status = parent->d_status;
   l->h_status = parent->h_status;
-  if (cudaStreamCreateWithFlags(&l->own_side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&l->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&l->ev_bulk, cudaEventDisableTiming) != cudaSuccess) {
-    delete l;
+  if (!create_factor_streams(l)) {
+    cdwac_destroy(l);
     return set_error(parent, CDWAC_ERR_CUDA, "lane creation failed");
   }
-  l->side_stream = l->own_side;
   l->freq_lanes = 1;
   *out = l;
   return CDWAC_OK;

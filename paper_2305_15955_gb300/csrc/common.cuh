@@ -60,9 +60,13 @@ struct cdwac_ctx {
   cudaStream_t side_stream = nullptr;  // second stream of the LDL^T lookahead (joined before each call returns)
   cudaStream_t own_side = nullptr;     // the side stream this context created (side_stream may be switched off)
   cudaEvent_t ev_panel = nullptr, ev_bulk = nullptr;
+  // the LDL^T critical path (panel, next-column update, diagonal block) runs on a high-priority stream so that its
+  // single-CTA launches are dispatched ahead of the bulk update's waiting CTAs (side stream, lowest priority)
+  cudaStream_t crit_stream = nullptr;
+  cudaEvent_t ev_crit_in = nullptr, ev_crit_out = nullptr;
   // batched launch: lane contexts (own scratch and streams, shared status word), fork/join events, graph cache
   bool is_lane = false;
-  int freq_lanes = 2;                   // concurrent frequency chains in the W builds (lanes never nest)
+  int freq_lanes = 8;                   // concurrent frequency chains in the W builds (lanes never nest)
   std::vector<cdwac_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_events;
@@ -118,6 +122,9 @@ struct Arena {
 };
 
 cdwac_status ensure_scratch(cdwac_ctx* ctx, size_t bytes);
+// Creates the LDL^T streams and events of a context (side stream, high-priority critical-path stream); false on
+// a CUDA error.
+bool create_factor_streams(cdwac_ctx* ctx);
 // batch.cu: lane contexts (own scratch, own side stream, the parent's status word) and their streams/events
 cdwac_status ensure_lanes(cdwac_ctx* ctx, int n);
 cdwac_status set_error(cdwac_ctx* ctx, cdwac_status st, const char* fmt, ...);
@@ -219,7 +226,10 @@ cdwac_status launch_transition_energies(cdwac_ctx* ctx, const double* eps, int n
                                         cudaStream_t st);
 // ldlt.cu
 template <class T>
-cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st);
+cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st,
+                         void* oz_scratch = nullptr);
+// Device scratch for ldlt_factor's tensor-core trailing update (oz_scratch; null = FP64 FMA update).
+size_t ldlt_tc_scratch_bytes(int n, bool cplx);
 template <class T>
 size_t ldlt_scratch_elems(int n);
 // W[s][m] = sum_P y_Pm^2 / d_P - sum_P o_Pm^2, y = L^{-1} o, for states s < n_states and columns

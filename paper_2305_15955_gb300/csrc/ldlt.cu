@@ -6,11 +6,13 @@
 // Blocked right-looking factorisation with NB = 64 column blocks, three launches per block step:
 //   diag  : one CTA factors the NB x NB diagonal block in shared memory and inverts its unit-lower L_kk;
 //   panel : rows below: W_ik = A_ik L_kk^-T, L_ik = W_ik D_k^-1 (W_ik kept in a panel buffer);
-//   update: trailing lower triangle A_ij -= W_ik L_jk^T.
+//   update: trailing lower triangle A_ij -= W_ik L_jk^T, with FP64 FMAs (update_kernel) or, given tensor-core
+//           scratch, as exact BF16 digit products on the tcgen05 tensor cores (ozaki.cu; FP64-equivalent).
 // Only the lower triangle of A is read or written.  A non-positive (real) or vanishing (complex) pivot sets
 // CDWAC_ERR_NOT_SPD / CDWAC_ERR_SINGULAR in the status word and the factorisation continues with a unit pivot,
 // so no NaN reaches later kernels.
 #include "common.cuh"
+#include "ozaki.cuh"
 
 __device__ inline double mkT(double v, double*) { return v; }
 __device__ inline cplx mkT(double v, cplx*) { return mkc(v, 0.0); }
@@ -61,11 +63,13 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
     T d = S[j * NB + j];
     const bool bad = bad_pivot(d);                   // same value in every thread
     if (bad) d = N::one();
-    const T rinv = N::div(N::one(), d);
-    for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
-      const T u = S[i * NB + j];
-      ucol[i] = u;
-      lcol[i] = N::mul(u, rinv);
+    if (j + 1 + tid < nb) {                          // only the threads that scale an entry form 1/d (FP64 is scarce)
+      const T rinv = N::div(N::one(), d);
+      for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
+        const T u = S[i * NB + j];
+        ucol[i] = u;
+        lcol[i] = N::mul(u, rinv);
+      }
     }
     __syncthreads();                                 // every thread has read the pivot; l and u are ready
     if (tid == 0) {
@@ -454,16 +458,23 @@ size_t ldlt_scratch_elems(int n) {
   return (size_t)n /*dinv*/ + (size_t)nblk * NB * NB /*linv*/ + 2 * (size_t)(nblk + 1) * NB * NB /*2 panels*/;
 }
 
-// Lookahead schedule on two streams (when the context owns a side stream): after panel k, the caller's stream
-// updates only the next block column, factors the next diagonal block and builds the next panel, while the side
-// stream updates the rest of the trailing matrix; the following step waits for both.  The panel buffer is
+// Lookahead schedule on two streams (when the context owns a side stream): after panel k, the critical-path
+// stream (high priority, forked from and joined back to the caller's stream) updates only the next block column,
+// factors the next diagonal block and builds the next panel, while the side stream (lowest priority) updates the
+// rest of the trailing matrix; the following step waits for both.  The panel buffer is
 // double-buffered because the side stream still reads panel k while panel k+1 is written.
 template <class T>
 static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel,
-                                          cudaStream_t st, size_t dsmem) {
+                                          cudaStream_t st, size_t dsmem, const OzakiPlan* oz) {
   const int nblk = (n + NB - 1) / NB;
   T* wp[2] = {wpanel, wpanel + (size_t)(nblk + 1) * NB * NB};
   cudaStream_t side = ctx->side_stream;
+  const cudaStream_t caller = st;
+  if (ctx->crit_stream) {   // the critical path moves to the high-priority stream, joined back at the end
+    st = ctx->crit_stream;
+    CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_crit_in, caller));
+    CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_crit_in, 0));
+  }
   {
     ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
     diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, 0, dinv, linv_blocks, ctx->d_status);
@@ -475,25 +486,36 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
   for (int kb = 0; kb < nblk - 1; ++kb) {
     const int k0 = kb * NB, rest = n - (k0 + NB), m = ceil_div(rest, 64);
     T* w = wp[kb & 1];
+    cdwac_status rc;
     {
       ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
       panel_kernel<T><<<ceil_div(rest, 16), 256, 0, st>>>(A, n, k0, dinv, linv_blocks, w);
       CDWAC_LAUNCH_CHECK(ctx);
+      // digit planes of this step (double-buffered like the panel: the side stream may still read step kb - 1)
+      if (oz && (rc = ozaki_slice<T>(ctx, *oz, kb & 1, A, n, k0, w, st))) return rc;
     }
     if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
     bulk_pending = false;
     if (m > 1) {
       CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_panel, st));
       CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_panel, 0));
-      update_kernel<T><<<m * (m - 1) / 2, 256, 0, side>>>(A, n, k0, w, 2);
-      CDWAC_LAUNCH_CHECK(ctx);
+      if (oz) {
+        if ((rc = ozaki_update<T>(ctx, *oz, kb & 1, A, n, k0, 2, side))) return rc;
+      } else {
+        update_kernel<T><<<m * (m - 1) / 2, 256, 0, side>>>(A, n, k0, w, 2);
+        CDWAC_LAUNCH_CHECK(ctx);
+      }
       CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_bulk, side));
       bulk_pending = true;
     }
     {
       ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
-      update_kernel<T><<<m, 256, 0, st>>>(A, n, k0, w, 1);
-      CDWAC_LAUNCH_CHECK(ctx);
+      if (oz) {
+        if ((rc = ozaki_update<T>(ctx, *oz, kb & 1, A, n, k0, 1, st))) return rc;
+      } else {
+        update_kernel<T><<<m, 256, 0, st>>>(A, n, k0, w, 1);
+        CDWAC_LAUNCH_CHECK(ctx);
+      }
     }
     {
       ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
@@ -502,15 +524,29 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
     }
   }
   if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
+  if (st != caller) {
+    CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_crit_out, st));
+    CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(caller, ctx->ev_crit_out, 0));
+  }
   return CDWAC_OK;
 }
 
+size_t ldlt_tc_scratch_bytes(int n, bool cplx) { return ozaki_scratch_bytes(n, cplx); }
+
 template <class T>
-cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st) {
+cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st,
+                         void* oz_scratch) {
   const size_t dsmem = 2 * NB * NB * sizeof(T);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+  OzakiPlan plan;
+  const OzakiPlan* oz = nullptr;
+  if (oz_scratch && n > NB) {
+    cdwac_status rc = ozaki_plan(ctx, oz_scratch, n, sizeof(T) == sizeof(cplx), &plan);
+    if (rc) return rc;
+    oz = &plan;
+  }
   if (ctx->side_stream && ctx->ev_panel && ctx->ev_bulk)
-    return ldlt_factor_lookahead<T>(ctx, A, n, dinv, linv_blocks, wpanel, st, dsmem);
+    return ldlt_factor_lookahead<T>(ctx, A, n, dinv, linv_blocks, wpanel, st, dsmem, oz);
   for (int k0 = 0; k0 < n; k0 += NB) {
     {
       ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
@@ -526,8 +562,14 @@ cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T
       CDWAC_LAUNCH_CHECK(ctx);
     }
     ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
-    update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel, 0);
-    CDWAC_LAUNCH_CHECK(ctx);
+    if (oz) {
+      cdwac_status rc;
+      if ((rc = ozaki_slice<T>(ctx, *oz, 0, A, n, k0, wpanel, st))) return rc;
+      if ((rc = ozaki_update<T>(ctx, *oz, 0, A, n, k0, 0, st))) return rc;
+    } else {
+      update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel, 0);
+      CDWAC_LAUNCH_CHECK(ctx);
+    }
   }
   return CDWAC_OK;
 }
@@ -556,8 +598,8 @@ template size_t ldlt_scratch_elems<double>(int);
 template size_t ldlt_scratch_elems<cplx>(int);
 template size_t quadform_scratch_elems<double>(int, int);
 template size_t quadform_scratch_elems<cplx>(int, int);
-template cdwac_status ldlt_factor<double>(cdwac_ctx*, double*, int, double*, double*, double*, cudaStream_t);
-template cdwac_status ldlt_factor<cplx>(cdwac_ctx*, cplx*, int, cplx*, cplx*, cplx*, cudaStream_t);
+template cdwac_status ldlt_factor<double>(cdwac_ctx*, double*, int, double*, double*, double*, cudaStream_t, void*);
+template cdwac_status ldlt_factor<cplx>(cdwac_ctx*, cplx*, int, cplx*, cplx*, cplx*, cudaStream_t, void*);
 template cdwac_status ldlt_quadform<double>(cdwac_ctx*, const double*, const double*, const double*, int,
                                             const void*, int, long, long, int, int, double*, long, double*,
                                             cudaStream_t);

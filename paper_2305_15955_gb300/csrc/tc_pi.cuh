@@ -7,7 +7,8 @@
 // per-lane region (the weighted planes of one frequency and the weights); tc_pi_scratch_bytes = both, laid out as
 // [shared | lane] with tc_pi_lane_part giving the lane part.
 size_t tc_pi_shared_bytes(int n_aux, long n_ov);
-size_t tc_pi_lane_bytes(int n_aux, long n_ov);
+// nacc = 1: a lane that only serves tc_pi_imag (one weighted pair); 2: also tc_pi_complex.
+size_t tc_pi_lane_bytes(int n_aux, long n_ov, int nacc = 2);
 size_t tc_pi_scratch_bytes(int n_aux, long n_ov);
 void* tc_pi_lane_part(void* scratch, int n_aux, long n_ov);
 // Splits O^{ia} into BF16 hi/lo planes in the shared region (once per call).

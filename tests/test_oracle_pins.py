@@ -234,3 +234,47 @@ def test_thiele_replay_of_greedy_order_is_identical(small):
     rep, record = o.thiele_replay(zc, Wc, fit.nodes)
     assert np.array_equal(rep.a, fit.a)
     assert all(take == emax for take, emax, _ in record)
+
+
+# ---- LDL^T without pivoting (Eq. bigLambda's factorisation) -------------------------------------------------------
+
+def test_ldlt_two_by_two_closed_form():
+    a, b, c = 3.0, 1.25, 2.0
+    L, d = o.ldlt_nopivot(np.array([[a, b], [b, c]]))
+    assert np.allclose(d, [a, c - b * b / a], rtol=0, atol=1e-15)
+    assert L[1, 0] == pytest.approx(b / a, abs=1e-16) and L[0, 0] == 1.0 and L[1, 1] == 1.0 and L[0, 1] == 0.0
+
+
+def test_ldlt_real_matches_library_cholesky(small):
+    import scipy.linalg
+    B = small["B"]
+    D = o.transition_energies(small["eps"], small["spec"].n_occ)
+    A = np.eye(B.shape[0]) - o.polarizability(B, D, 0.7j).real
+    L, d = o.ldlt_nopivot(A)
+    C = scipy.linalg.cholesky(A, lower=True)
+    assert np.all(d > 0)
+    assert np.max(np.abs(L * np.sqrt(d)[None, :] - C)) < 1e-13 * np.max(np.abs(C))
+
+
+def test_ldlt_complex_symmetric_solves_like_library(small):
+    B = small["B"]
+    D = o.transition_energies(small["eps"], small["spec"].n_occ)
+    A = np.eye(B.shape[0]) - o.polarizability(B, D, 0.31 + 1e-3j)
+    L, d = o.ldlt_nopivot(A)
+    assert np.max(np.abs((L * d[None, :]) @ L.T - A)) < 1e-12 * np.max(np.abs(A))
+    b = np.cos(np.arange(A.shape[0]) * 0.37) + 1j * np.sin(np.arange(A.shape[0]) * 0.11)
+    import scipy.linalg
+    y = scipy.linalg.solve_triangular(L, b, lower=True, unit_diagonal=True)
+    x = scipy.linalg.solve_triangular(L.T, y / d, lower=False, unit_diagonal=True)
+    ref = np.linalg.solve(A, b)
+    assert np.max(np.abs(x - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_ldlt_reads_only_the_lower_triangle():
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((40, 40))
+    A = np.eye(40) * 40 + X @ X.T
+    Ag = np.tril(A) + np.triu(rng.standard_normal((40, 40)), 1)   # garbage above the diagonal
+    L1, d1 = o.ldlt_nopivot(A)
+    L2, d2 = o.ldlt_nopivot(Ag)
+    assert np.array_equal(L1, L2) and np.array_equal(d1, d2)
