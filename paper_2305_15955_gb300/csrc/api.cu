@@ -347,14 +347,14 @@ struct ImagBufs {
 };
 
 // FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: FP32 solves of the
-// same form on the tensor-core Pi (wsolve32).
+// same form with tensor-core products on the tensor-core Pi (wsolve_tc).
 static size_t imag_lane_bytes(const cdwac_system* sys, bool mixed) {
   const int n = sys->n_aux, nb = sys->n_basis, cols = sys->n_states * nb;
   const long n_ov = (long)sys->n_occ * (nb - sys->n_occ);
   size_t b = factor_scratch_bytes<double>(n, cols, mixed ? 0 : 2) + 4096;
   if (!mixed) b += sizeof(double) * ((size_t)n + (size_t)sys->n_states * n * nb);
   if (mixed)
-    b += tc_pi_lane_bytes(n, n_ov, 1) + sizeof(float) * (size_t)n * n + wsolve32_scratch_bytes(n, cols) +
+    b += tc_pi_lane_bytes(n, n_ov, 1) + sizeof(float) * (size_t)n * n + wsolve_tc_scratch_bytes(n, cols) +
          ldlt_tc_scratch_bytes(n, false) + 1280;
   return b;
 }
@@ -368,7 +368,7 @@ static ImagBufs carve_imag(Arena& ar, const cdwac_system* sys, bool mixed) {
   b.V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
   b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov, 1)) : nullptr;
   b.negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
-  b.ws32 = mixed ? ar.take<char>(wsolve32_scratch_bytes(n, cols)) : nullptr;
+  b.ws32 = mixed ? ar.take<char>(wsolve_tc_scratch_bytes(n, cols)) : nullptr;
   b.oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, false)) : nullptr;
   return b;
 }
@@ -394,7 +394,7 @@ static cdwac_status imag_freqs(cdwac_ctx* lc, const cdwac_system* sys, const cdw
     }
     ProfScope ps(lc, PROF_QUADFORM, st);
     if (mixed) {
-      rc = wsolve32(lc, b.f.A, b.f.dinv, b.f.linv, b.negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
+      rc = wsolve_tc(lc, b.f.A, b.f.dinv, b.f.linv, b.negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
                     sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, b.ws32, st);
     } else {
       if ((rc = launch_pi_times_o(lc, b.f.A, b.pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,

@@ -246,7 +246,13 @@ size_t quadform_scratch_elems(int n, int n_cols);
 cdwac_status ldlt_quadform_pi(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv_blocks, int n,
                               const void* O, int dtype, const double* V, long o_state_stride, long ld_o, int n_states,
                               int cols_per_state, double* W_out, long w_state_stride, double* ywork, cudaStream_t st);
-// wsolve32.cu: mixed-precision W = sum_P y u / d (y = L^-1 o, u = L^-1 Pi o in FP32), Pi from negpi32 (-Pi lower, FP32)
+// wsolve_tc.cu: mixed-precision W = sum_P y u / d, [y | u] = L^-1 [o | Pi o] as a blocked forward substitution whose
+// products run on the tensor cores (split BF16, FP32 sums); Pi from negpi32 (-Pi, FP32, full symmetric).
+size_t wsolve_tc_scratch_bytes(int n, int n_cols);
+cdwac_status wsolve_tc(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
+                       int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,
+                       int cols_per_state, double* W_out, long w_state_stride, void* scratch, cudaStream_t st);
+// wsolve32.cu: the same W on the CUDA cores (y = L^-1 o, u = L^-1 Pi o in FP32)
 size_t wsolve32_scratch_bytes(int n, int n_cols);
 cdwac_status wsolve32(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
                       int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,

@@ -496,8 +496,18 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
     }
     if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
     bulk_pending = false;
+    if (m > 1) CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_panel, st));
+    {
+      // the next block column first: its CTAs are queued ahead of the bulk update's
+      ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
+      if (oz) {
+        if ((rc = ozaki_update<T>(ctx, *oz, kb & 1, A, n, k0, 1, st))) return rc;
+      } else {
+        update_kernel<T><<<m, 256, 0, st>>>(A, n, k0, w, 1);
+        CDWAC_LAUNCH_CHECK(ctx);
+      }
+    }
     if (m > 1) {
-      CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_panel, st));
       CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(side, ctx->ev_panel, 0));
       if (oz) {
         if ((rc = ozaki_update<T>(ctx, *oz, kb & 1, A, n, k0, 2, side))) return rc;
@@ -507,15 +517,6 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
       }
       CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_bulk, side));
       bulk_pending = true;
-    }
-    {
-      ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
-      if (oz) {
-        if ((rc = ozaki_update<T>(ctx, *oz, kb & 1, A, n, k0, 1, st))) return rc;
-      } else {
-        update_kernel<T><<<m, 256, 0, st>>>(A, n, k0, w, 1);
-        CDWAC_LAUNCH_CHECK(ctx);
-      }
     }
     {
       ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);

@@ -1,0 +1,398 @@
+// Mixed-precision W projection on the tcgen05 tensor cores, imaginary axis (Eqs. wriv, bigLambda):
+//
+//   W_nm = o^T (I - Pi)^-1 Pi o = sum_P y_P u_P / d_P,   [y | u] = L^-1 [o | Pi o],   L D L^T = I - Pi.
+//
+// The right-hand sides of all columns m (every state, every orbital) are solved together as one blocked forward
+// substitution over the 64-row blocks b of the factor:
+//
+//   T = [O | Pi O]                              split-BF16 tensor-core GEMM for Pi O (three products, FP32 sums)
+//   for b:  Y_b = L_bb^-1 T_b                   CUDA cores, FP32 (64 x 64 times 64 x 2C), W partial sums in FP64
+//           T_>b -= L_>b,b Y_b                  split-BF16 tensor-core GEMM with K = 64
+//
+// T is held column-major (T[col][row], col < 2C) so that both the GEMM epilogue (a warp writes 32 consecutive rows
+// of one column) and the block solve (64 consecutive rows of a column) touch contiguous memory.  The BF16 planes of
+// the factor, of Pi and of O^T are K-major for TMA (128-byte swizzle); the planes of Y_b are [2C][64].  The
+// products carry ~2^-16 relative error per term like the tensor-core Pi, which dominates the mixed path's error.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include "common.cuh"
+#include "tcgen05.cuh"
+
+namespace {
+using namespace tc;
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int PLANE = BM * BK * 2;       // bytes of one 128 x 64 BF16 tile
+constexpr int STAGES = 3;
+constexpr int STAGE = 4 * PLANE;         // A hi, A lo, B hi, B lo
+constexpr int SMEM = STAGES * STAGE + 1024;
+constexpr int TMEM_COLS = 128;
+
+struct GemmMaps {
+  CUtensorMap ah, al, bh, bl;
+};
+
+// out[(col) * ld + row_off + row] (=, -=) sum_k A[a_y0 + row][a_x0 + k] B[b_y0 + col][k],  row < M, col < N.
+template <bool SUB>
+__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ GemmMaps maps, int M, int N,
+                                                         int k_tiles, int a_x0, int a_y0, int b_y0, float* out,
+                                                         long ld, int row_off, unsigned* status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, consumed;
+
+  const int mt = (M + BM - 1) / BM;
+  const int tm = blockIdx.x % mt, tn = blockIdx.x / mt;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], (uint32_t)STAGE);
+      uint8_t* st = smem + s * STAGE;
+      const int x = a_x0 + kt * BK;
+      tma_load_2d(&maps.ah, &full_bar[s], st + 0 * PLANE, x, a_y0 + tm * BM);
+      tma_load_2d(&maps.al, &full_bar[s], st + 1 * PLANE, x, a_y0 + tm * BM);
+      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * PLANE, kt * BK, b_y0 + tn * BN);
+      tma_load_2d(&maps.bl, &full_bar[s], st + 3 * PLANE, kt * BK, b_y0 + tn * BN);
+    }
+    issued = kt;
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * STAGE);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t ko = kk * 32;
+        const uint64_t ah = sdesc(base + 0 * PLANE + ko), al = sdesc(base + 1 * PLANE + ko);
+        const uint64_t bh = sdesc(base + 2 * PLANE + ko), bl = sdesc(base + 3 * PLANE + ko);
+        umma(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        umma(tmem, ah, bl, idesc, 1u);
+        umma(tmem, al, bh, idesc, 1u);
+      }
+      umma_commit(&empty_bar[s]);
+    }
+    consumed = kt;
+    umma_commit(&done_bar);
+  }
+  __syncwarp();
+
+  const bool done_ok = mbar_wait(&done_bar, 0, nullptr);
+  tc_fence_after();
+  __syncthreads();
+  if (threadIdx.x == 0 && (!done_ok || abort_flag)) {
+    raise_status(status, DEV_ERR_TIMEOUT);
+    for (int kt = consumed; kt < issued; ++kt) mbar_wait(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, nullptr);
+  }
+  if (done_ok && !abort_flag) {
+    const int row = tm * BM + warp * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + lane_base + c0, v);
+      if (row < M) {
+        float* o = out + row_off + row;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = tn * BN + c0 + j;
+          if (col < N) {
+            if (SUB)
+              o[(long)col * ld] -= __uint_as_float(v[j]);
+            else
+              o[(long)col * ld] = __uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// Strict lower triangle of the FP64 factor -> BF16 hi/lo planes [n][npad] (zero elsewhere, including the K
+// padding); the diagonal-block inverses -> FP32.
+__global__ void factor_split_kernel(const double* __restrict__ L, int n, int npad, const double* __restrict__ linv,
+                                    int nblk, __nv_bfloat16* __restrict__ lh, __nv_bfloat16* __restrict__ ll,
+                                    float* __restrict__ linv32) {
+  const long total = (long)n * npad, tl = (long)nblk * 64 * 64;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total + tl; e += (long)gridDim.x * blockDim.x) {
+    if (e < total) {
+      const long r = e / npad, c = e % npad;
+      const float v = (c < r) ? (float)L[r * n + c] : 0.f;
+      split_bf16(v, lh[e], ll[e]);
+    } else {
+      linv32[e - total] = (float)linv[e - total];
+    }
+  }
+}
+
+// Pi = -negpi (FP32, full symmetric [n][n]) -> BF16 hi/lo planes [n][npad]
+__global__ void pi_split_kernel(const float* __restrict__ negpi, int n, int npad, __nv_bfloat16* __restrict__ ph,
+                                __nv_bfloat16* __restrict__ pl) {
+  const long total = (long)n * npad;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+    const long r = e / npad, c = e % npad;
+    const float v = c < n ? -negpi[r * n + c] : 0.f;
+    split_bf16(v, ph[e], pl[e]);
+  }
+}
+
+// O^T: column c = (state s, orbital m) -> FP32 row T[c][0..n) (zero padded to npad) and its BF16 hi/lo planes
+template <class TIn>
+__global__ void o_transpose_kernel(const TIn* __restrict__ O, long o_state_stride, long ld_o, int cols_per_state,
+                                   int n_cols, int n, int npad, float* __restrict__ t32, __nv_bfloat16* __restrict__ oh,
+                                   __nv_bfloat16* __restrict__ ol) {
+  __shared__ float tile[32][33];
+  const int P0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;   // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int P = P0 + k, c = c0 + tx;
+    float v = 0.f;
+    if (P < n && c < n_cols) {
+      const int s = c / cols_per_state, m = c % cols_per_state;
+      v = (float)O[s * o_state_stride + (long)P * ld_o + m];
+    }
+    tile[k][tx] = v;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, P = P0 + tx;
+    if (c < n_cols && P < npad) {
+      const float v = tile[tx][k];
+      const long e = (long)c * npad + P;
+      t32[e] = v;
+      split_bf16(v, oh[e], ol[e]);
+    }
+  }
+}
+
+// Block step b: Y_b = X_b T_b for every column (X_b = L_bb^-1, unit lower), written as BF16 hi/lo planes
+// [2C][64] for the next update, and the W partial sums  part[b][m] = sum_r y[m][r] y[C + m][r] / d_r.
+// One CTA per 16 column pairs (m, C + m); thread (r, g) owns row r and columns {4 of m, their 4 partners}.
+constexpr int SP = 16;
+__global__ void __launch_bounds__(256) block_solve_kernel(const float* __restrict__ T, long ld, int n, int C, int b,
+                                                          const float* __restrict__ linv32,
+                                                          const double* __restrict__ dinv,
+                                                          __nv_bfloat16* __restrict__ yh,
+                                                          __nv_bfloat16* __restrict__ yl,
+                                                          double* __restrict__ part) {
+  __shared__ float Xs[64][65];
+  __shared__ float Ts[2 * SP][65];
+  __shared__ double red[4][64][4];
+  const int m0 = blockIdx.x * SP;
+  const int tid = threadIdx.x, r = tid % 64, g = tid / 64;
+  const int r0 = b * 64;
+  const float* X = linv32 + (long)b * 64 * 64;
+  for (int e = tid; e < 64 * 64; e += 256) Xs[e / 64][e % 64] = X[e];
+  for (int e = tid; e < 2 * SP * 64; e += 256) {
+    const int cc = e / 64, k = e % 64;
+    const int col = cc < SP ? m0 + cc : C + m0 + (cc - SP);
+    const bool ok = (cc < SP ? m0 + cc : m0 + cc - SP) < C && r0 + k < n;
+    Ts[cc][k] = ok ? T[(long)col * ld + r0 + k] : 0.f;
+  }
+  __syncthreads();
+  float y[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) y[j] = 0.f;
+  for (int k = 0; k <= r; ++k) {
+    const float x = Xs[r][k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      y[j] = fmaf(x, Ts[g * 4 + j][k], y[j]);
+      y[4 + j] = fmaf(x, Ts[SP + g * 4 + j][k], y[4 + j]);
+    }
+  }
+  const int row = r0 + r;
+  const double di = row < n ? dinv[row] : 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int m = m0 + g * 4 + j;
+    red[g][r][j] = (double)y[j] * (double)y[4 + j] * di;
+    if (m < C) {
+      __nv_bfloat16 h, l;
+      split_bf16(y[j], h, l);
+      yh[(long)m * 64 + r] = h;
+      yl[(long)m * 64 + r] = l;
+      split_bf16(y[4 + j], h, l);
+      yh[(long)(C + m) * 64 + r] = h;
+      yl[(long)(C + m) * 64 + r] = l;
+    }
+  }
+  __syncthreads();
+  if (tid < SP) {
+    const int gg = tid / 4, j = tid % 4, m = m0 + tid;
+    double s = 0.0;
+    for (int k = 0; k < 64; ++k) s += red[gg][k][j];
+    if (m < C) part[(long)b * C + m] = s;
+  }
+}
+
+// W[c] = sum_b part[b][c], written to W_out[s * w_state_stride + m] for c = (s, m)
+__global__ void w_reduce_kernel(const double* __restrict__ part, int nblk, int C, int cols_per_state,
+                                double* __restrict__ W_out, long w_state_stride) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(long)b * C + c];
+  W_out[(long)(c / cols_per_state) * w_state_stride + c % cols_per_state] = s;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rows, long kpad) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+struct Bufs {
+  __nv_bfloat16 *lh, *ll, *ph, *pl, *oh, *ol, *yh, *yl;
+  float *t, *linv32;
+  double* part;
+  int npad, nblk;
+};
+
+Bufs carve(void* scratch, int n, int C) {
+  Bufs b;
+  b.npad = ((n + 63) / 64) * 64;
+  b.nblk = (n + 63) / 64;
+  Arena ar(scratch);
+  const size_t sq = (size_t)n * b.npad, oc = (size_t)C * b.npad;
+  b.lh = ar.take<__nv_bfloat16>(sq);
+  b.ll = ar.take<__nv_bfloat16>(sq);
+  b.ph = ar.take<__nv_bfloat16>(sq);
+  b.pl = ar.take<__nv_bfloat16>(sq);
+  b.oh = ar.take<__nv_bfloat16>(oc);
+  b.ol = ar.take<__nv_bfloat16>(oc);
+  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 64);
+  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 64);
+  b.t = ar.take<float>(2 * oc);
+  b.linv32 = ar.take<float>((size_t)b.nblk * 64 * 64);
+  b.part = ar.take<double>((size_t)b.nblk * C);
+  return b;
+}
+
+int grid_of(cdwac_ctx* ctx, long work) {
+  long b = (work + 255) / 256, cap = (long)ctx->num_sms * 8;
+  return (int)(b < 1 ? 1 : (b < cap ? b : cap));
+}
+
+template <bool SUB>
+cdwac_status gemm(cdwac_ctx* ctx, const GemmMaps& maps, int M, int N, int k_tiles, int a_x0, int a_y0, float* out,
+                  long ld, int row_off, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return CDWAC_OK;
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_gemm_kernel<SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
+  const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+  tc_gemm_kernel<SUB><<<mt * nt, 128, SMEM, st>>>(maps, M, N, k_tiles, a_x0, a_y0, 0, out, ld, row_off,
+                                                  ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+}  // namespace
+
+size_t wsolve_tc_scratch_bytes(int n, int n_cols) {
+  const size_t npad = ((size_t)n + 63) / 64 * 64, nblk = npad / 64;
+  const size_t sq = (size_t)n * npad, oc = (size_t)n_cols * npad;
+  return 4 * (sq * 2 + 256) + 2 * (oc * 2 + 256) + 2 * ((size_t)2 * n_cols * 64 * 2 + 256) + (2 * oc * 4 + 256) +
+         (nblk * 64 * 64 * 4 + 256) + (nblk * n_cols * 8 + 256) + 1024;
+}
+
+cdwac_status wsolve_tc(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
+                       int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,
+                       int cols_per_state, double* W_out, long w_state_stride, void* scratch, cudaStream_t st) {
+  const int C = n_states * cols_per_state;
+  if (C <= 0) return CDWAC_OK;
+  Bufs b = carve(scratch, n, C);
+  const long ld = b.npad;
+  {
+    const long work = (long)n * b.npad + (long)b.nblk * 4096;
+    factor_split_kernel<<<grid_of(ctx, work), 256, 0, st>>>(L, n, b.npad, linv, b.nblk, b.lh, b.ll, b.linv32);
+    CDWAC_LAUNCH_CHECK(ctx);
+    pi_split_kernel<<<grid_of(ctx, (long)n * b.npad), 256, 0, st>>>(negpi32, n, b.npad, b.ph, b.pl);
+    CDWAC_LAUNCH_CHECK(ctx);
+    dim3 tg((b.npad + 31) / 32, (C + 31) / 32);
+    if (dtype == CDWAC_F64)
+      o_transpose_kernel<double><<<tg, 256, 0, st>>>((const double*)O, o_state_stride, ld_o, cols_per_state, C, n,
+                                                     b.npad, b.t, b.oh, b.ol);
+    else
+      o_transpose_kernel<float><<<tg, 256, 0, st>>>((const float*)O, o_state_stride, ld_o, cols_per_state, C, n,
+                                                    b.npad, b.t, b.oh, b.ol);
+    CDWAC_LAUNCH_CHECK(ctx);
+  }
+  GemmMaps pio, upd;
+  if (!make_map(&pio.ah, b.ph, n, b.npad) || !make_map(&pio.al, b.pl, n, b.npad) ||
+      !make_map(&pio.bh, b.oh, C, b.npad) || !make_map(&pio.bl, b.ol, C, b.npad) ||
+      !make_map(&upd.ah, b.lh, n, b.npad) || !make_map(&upd.al, b.ll, n, b.npad) ||
+      !make_map(&upd.bh, b.yh, 2 * C, 64) || !make_map(&upd.bl, b.yl, 2 * C, 64))
+    return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the W solve (n=%d, C=%d)", n, C);
+  cdwac_status rc;
+  // second half of T: Pi O
+  if ((rc = gemm<false>(ctx, pio, n, C, b.npad / BK, 0, 0, b.t + (long)C * ld, ld, 0, st))) return rc;
+  for (int blk = 0; blk < b.nblk; ++blk) {
+    block_solve_kernel<<<(C + SP - 1) / SP, 256, 0, st>>>(b.t, ld, n, C, blk, b.linv32, dinv, b.yh, b.yl, b.part);
+    CDWAC_LAUNCH_CHECK(ctx);
+    const int r1 = (blk + 1) * 64;
+    if (r1 < n && (rc = gemm<true>(ctx, upd, n - r1, 2 * C, 1, blk * 64, r1, b.t, ld, r1, st))) return rc;
+  }
+  w_reduce_kernel<<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, cols_per_state, W_out, w_state_stride);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
