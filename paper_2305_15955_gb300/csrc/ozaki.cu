@@ -31,6 +31,8 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "ozaki.cuh"
 #include "tcgen05.cuh"
 
@@ -182,11 +184,24 @@ __global__ void __launch_bounds__(128, 1) oz_update_kernel(const __grid_constant
     if (loads_issued & 2) mbar_wait(&bar_a1, 0, nullptr);
   }
   if (good) {
-    // every MMA has completed, so the operand buffers are free: stage [part][warp][32 rows][33] doubles
+    // every MMA has completed, so the operand buffers are free: stage [part][warp][32 rows][33] doubles.
+    // Warp w owns tile rows 32w..32w+31; in the read-modify-write lane = column, so each row segment is one
+    // coalesced access.  The A values are fetched in two halves of 16 rows: the first before the tensor-memory
+    // drain (its latency hides behind the integer recombination), the second before the first is written back.
+    using T = typename std::conditional<CPLX, cplx, double>::type;
+    T* Ab = reinterpret_cast<T*>(A_out);
     double* stage = reinterpret_cast<double*>(smem);
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const int rbase = row0 + warp * 32;
 #pragma unroll 1
     for (int c0 = 0; c0 < BN; c0 += 32) {
+      const int col = col0 + c0 + lane;
+      T cv0[16], cv1[16];
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const int row = rbase + rr;
+        if (row < n && col <= row) cv0[rr] = Ab[(long)row * n + col];
+      }
 #pragma unroll 1
       for (int p = 0; p < C::NPART; ++p) {
         // exact integer recombination N = sum_L acc_L 2^(SH - 7L) on the integer pipe (bits of the lowest levels
@@ -212,25 +227,29 @@ __global__ void __launch_bounds__(128, 1) oz_update_kernel(const __grid_constant
         for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __ll2double_rn(acc[j]);
       }
       __syncwarp();
-      // lane = column: each row segment is one coalesced read-modify-write
-      const int col = col0 + c0 + lane;
+#pragma unroll
+      for (int rr = 0; rr < 16; ++rr) {
+        const int row = rbase + 16 + rr;
+        if (row < n && col <= row) cv1[rr] = Ab[(long)row * n + col];
+      }
       const double sl = scale_l[c0 + lane] * ldexp(1.0, -C::SHIFT);   // exact: powers of two
       const double* st0 = stage + (warp * 32) * 33;
       const double* st1 = stage + ((4 + warp) * 32) * 33;
-#pragma unroll 4
-      for (int rr = 0; rr < 32; ++rr) {
-        const int row = row0 + warp * 32 + rr;
-        if (row < n && col <= row) {
-          const double sc = scale_w[warp * 32 + rr] * sl;
-          if (!CPLX) {
-            double* p = reinterpret_cast<double*>(A_out) + (long)row * n + col;
-            *p = fma(-st0[rr * 33 + lane], sc, *p);
-          } else {
-            cplx* p = reinterpret_cast<cplx*>(A_out) + (long)row * n + col;
-            cplx v = *p;
-            v.x = fma(-st0[rr * 33 + lane], sc, v.x);
-            v.y = fma(-st1[rr * 33 + lane], sc, v.y);
-            *p = v;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+          const int r = h * 16 + rr, row = rbase + r;
+          if (row < n && col <= row) {
+            const double sc = scale_w[warp * 32 + r] * sl;
+            T v = h == 0 ? cv0[rr] : cv1[rr];
+            if constexpr (!CPLX) {
+              v = fma(-st0[r * 33 + lane], sc, v);
+            } else {
+              v.x = fma(-st0[r * 33 + lane], sc, v.x);
+              v.y = fma(-st1[r * 33 + lane], sc, v.y);
+            }
+            Ab[(long)row * n + col] = v;
           }
         }
       }
