@@ -4,10 +4,12 @@
 // complex symmetric A (near-real points and residues; no conjugation, no pivoting).
 //
 // Blocked right-looking factorisation with NB = 64 column blocks, three launches per block step:
-//   diag  : one CTA factors the NB x NB diagonal block in shared memory and inverts its unit-lower L_kk;
-//   panel : rows below: W_ik = A_ik L_kk^-T, L_ik = W_ik D_k^-1 (W_ik kept in a panel buffer);
+//   diag  : one CTA factors the NB x NB diagonal block in shared memory;
+//   panel : rows below: W_ik = A_ik L_kk^-T by forward substitution, L_ik = W_ik D_k^-1 (W_ik kept in a panel
+//           buffer);
 //   update: trailing lower triangle A_ij -= W_ik L_jk^T, with FP64 FMAs (update_kernel) or, given tensor-core
 //           scratch, as exact BF16 digit products on the tcgen05 tensor cores (ozaki.cu; FP64-equivalent).
+// After the last step one launch inverts every unit-lower diagonal block L_kk (the blocked solves use them).
 // Only the lower triangle of A is read or written.  A non-positive (real) or vanishing (complex) pivot sets
 // CDWAC_ERR_NOT_SPD / CDWAC_ERR_SINGULAR in the status word and the factorisation continues with a unit pivot,
 // so no NaN reaches later kernels.
@@ -41,116 +43,151 @@ __device__ inline unsigned pivot_err(double) { return DEV_ERR_NOT_SPD; }
 __device__ inline unsigned pivot_err(cplx) { return DEV_ERR_SINGULAR; }
 
 // ---- diagonal block --------------------------------------------------------------------------------------
-// One CTA (256 threads as 16 x 16) factors the NB x NB block held in shared memory: step j scales column j by
-// the reciprocal pivot (one division per thread per step) and updates the trailing triangle with l_i * u_k
-// (u = the unscaled column).  The unit-lower inverse X = L_kk^-1 is then built row by row, four threads per
-// column sharing each dot product.
+// One CTA (256 threads) factors the NB x NB block held in shared memory (row stride NB + 1).  Step j: the threads
+// of rows i > j scale column j by 1/d_j (only they evaluate the pivot; GB300's FP64 units are scarce), then the
+// trailing triangle j < k <= i is updated with l_i u_k (u = the unscaled column).  The triangle's elements are
+// numbered by k from the last column down and i upwards, so that the elements of step j are the first
+// (63 - j)(64 - j) / 2 numbers: every lane of every warp has work until the last steps.
+__device__ inline bool bad_pivot_fast(double d) { return !(d > 0.0); }
+__device__ inline bool bad_pivot_fast(cplx d) { return !(fabs(d.x) + fabs(d.y) > 1e-300); }
+
+constexpr int SD = NB + 1;                 // shared-memory row stride of the diagonal block
+constexpr int TRI = NB * (NB - 1) / 2;     // elements j < k <= i < NB of the first step, the largest
+constexpr int PER_THREAD = (TRI + 255) / 256;
+
 template <class T>
-__global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv, T* linv, unsigned* status) {
+__global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv, unsigned* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* S = reinterpret_cast<T*>(smem_raw);            // [NB][NB]
-  T* X = S + NB * NB;                                // [NB][NB] inverse of unit-lower L_kk
+  T* S = reinterpret_cast<T*>(smem_raw);            // [NB][SD]
   __shared__ T lcol[NB], ucol[NB];
+  __shared__ int bad_step;
   using N = Num<T>;
   const int nb = min(NB, n - k0);
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int tid = threadIdx.x;
   for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int i = e / NB, j = e % NB;
-    S[e] = (i < nb && j <= i) ? A[(long)(k0 + i) * n + (k0 + j)] : (i == j ? N::one() : N::zero());
+    const int i = e / NB, j = e % NB;
+    S[i * SD + j] = (i < nb && j <= i) ? A[(long)(k0 + i) * n + (k0 + j)] : (i == j ? N::one() : N::zero());
+  }
+  // this thread's trailing-triangle elements: number e -> (i, k), u = 63 - k, e in [u(u+1)/2, u(u+1)/2 + u]
+  short ti[PER_THREAD], tk[PER_THREAD];
+#pragma unroll
+  for (int q = 0; q < PER_THREAD; ++q) {
+    const int e = tid + 256 * q;
+    int u = (int)((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+    while ((u + 1) * (u + 2) / 2 <= e) ++u;
+    while (u * (u + 1) / 2 > e) --u;
+    tk[q] = (short)(NB - 1 - u);
+    ti[q] = (short)(NB - 1 - u + (e - u * (u + 1) / 2));
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    T d = S[j * NB + j];
-    const bool bad = bad_pivot(d);                   // same value in every thread
-    if (bad) d = N::one();
-    if (j + 1 + tid < nb) {                          // only the threads that scale an entry form 1/d (FP64 is scarce)
-      const T rinv = N::div(N::one(), d);
-      for (int i = j + 1 + tid; i < nb; i += blockDim.x) {
-        const T u = S[i * NB + j];
-        ucol[i] = u;
-        lcol[i] = N::mul(u, rinv);
+    if (tid < NB) {
+      const T d0 = S[j * SD + j];
+      const bool bad = bad_pivot_fast(d0);
+      if (tid == 0) bad_step = bad ? 1 : 0;
+      if (tid > j && tid < nb) {
+        const T rinv = N::div(N::one(), bad ? N::one() : d0);
+        const T u = S[tid * SD + j];
+        ucol[tid] = u;
+        lcol[tid] = N::mul(u, rinv);
       }
     }
-    __syncthreads();                                 // every thread has read the pivot; l and u are ready
-    if (tid == 0) {
-      if (bad) {
-        raise_status(status, pivot_err(S[j * NB + j]));
-        S[j * NB + j] = N::one();
-      }
+    __syncthreads();                                 // pivot read by every thread that needs it; l and u ready
+    if (tid == 0 && bad_step) {
+      raise_status(status, pivot_err(S[j * SD + j]));
+      S[j * SD + j] = N::one();
     }
-    for (int i = j + 1 + ty; i < nb; i += 16) {
-      const T li = lcol[i];
-      for (int k = j + 1 + tx; k <= i; k += 16) S[i * NB + k] = N::fms(li, ucol[k], S[i * NB + k]);
-      if (tx == 0) S[i * NB + j] = li;
+    if (tid > j && tid < nb) S[tid * SD + j] = lcol[tid];
+    const int count = (NB - 1 - j) * (NB - j) / 2;   // elements with k > j
+#pragma unroll
+    for (int q = 0; q < PER_THREAD; ++q) {
+      const int e = tid + 256 * q;
+      const int i = ti[q], k = tk[q];
+      if (e < count && i < nb) S[i * SD + k] = N::fms(lcol[i], ucol[k], S[i * SD + k]);
     }
     __syncthreads();
   }
-  // X = L_kk^{-1}: X[c][c] = 1, X[i][c] = -sum_{c <= t < i} L[i][t] X[t][c]; thread (c, part) sums t = c + part mod 4
-  {
-    const int c = tid / 4, part = tid % 4;
-    for (int i = 0; i < NB; ++i)
-      if (part == 0) X[i * NB + c] = (i == c && c < nb) ? N::one() : N::zero();
-    __syncwarp();
-    for (int i = 1; i < nb; ++i) {                  // uniform trip count: the shuffles need the whole warp
-      const bool active = c < i;
-      T s = N::zero();
-      if (active)
-        for (int t = c + part; t < i; t += 4) s = N::fma_(S[i * NB + t], X[t * NB + c], s);
-      s = N::add(s, shfl_xor_T(s, 1));
-      s = N::add(s, shfl_xor_T(s, 2));
-      if (active && part == 0) X[i * NB + c] = N::sub(N::zero(), s);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  const int kb = k0 / NB;
   for (int e = tid; e < NB * NB; e += blockDim.x) {
-    int i = e / NB, j = e % NB;
-    linv[(long)kb * NB * NB + e] = X[e];
-    if (i < nb && j <= i) A[(long)(k0 + i) * n + (k0 + j)] = S[e];   // diagonal holds d_i
+    const int i = e / NB, j = e % NB;
+    if (i < nb && j <= i) A[(long)(k0 + i) * n + (k0 + j)] = S[i * SD + j];   // diagonal holds d_i
   }
-  for (int i = tid; i < nb; i += blockDim.x) dinv[k0 + i] = N::div(N::one(), S[i * NB + i]);
+  if (tid < nb) dinv[k0 + tid] = N::div(N::one(), S[tid * SD + tid]);
 }
 
-// ---- panel: W_i = A_i L_kk^-T, L_i = W_i D^-1 for 16 rows below the diagonal block per CTA ---------------
+// ---- inverses of the unit-lower diagonal blocks, for the solves after the factorisation ------------------------
+// One CTA per block: X = L_kk^-1, X[c][c] = 1, X[i][c] = -sum_{c <= t < i} L[i][t] X[t][c]; thread (c, part)
+// sums t = c + part mod 4.
 template <class T>
-__global__ void __launch_bounds__(256) panel_kernel(T* A, int n, int k0, const T* dinv, const T* linv, T* wpanel) {
-  __shared__ T Xs[TK][TP];       // chunk of (L_kk^-1)^T: Xs[c - c0][j] = Linv[j][c]
-  __shared__ T As[TK][17];       // chunk of the panel rows: As[c - c0][r]
+__global__ void __launch_bounds__(256) inverse_kernel(const T* A, int n, T* linv) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);            // [NB][NB] strict lower part of the block
+  T* X = S + NB * NB;
   using N = Num<T>;
-  const int nb = min(NB, n - k0);
-  const int r0 = k0 + NB + blockIdx.x * 16;
-  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int kb = k0 / NB;
-  T acc[4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j] = N::zero();
-  for (int c0 = 0; c0 < nb; c0 += TK) {
-    {
-      const int cc = tid % TK, r = tid / TK;       // 256 threads = 16 rows x 16 columns of the chunk
-      const int c = c0 + cc, row = r0 + r;
-      As[cc][r] = (row < n && c < nb) ? A[(long)row * n + k0 + c] : N::zero();
-    }
-    for (int e = tid; e < TK * 64; e += 256) {
-      const int cc = e % TK, j = e / TK, c = c0 + cc;
-      Xs[cc][j] = (c < nb) ? linv[(long)kb * NB * NB + (long)j * NB + c] : N::zero();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < TK; ++q) {
-      const T a = As[q][ty];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[j] = N::fma_(a, Xs[q][tx * 4 + j], acc[j]);
-    }
-    __syncthreads();
+  const int k0 = blockIdx.x * NB, nb = min(NB, n - k0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < NB * NB; e += blockDim.x) {
+    const int i = e / NB, j = e % NB;
+    S[e] = (i < nb && j < i) ? A[(long)(k0 + i) * n + (k0 + j)] : N::zero();
   }
-  const int row = r0 + ty;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int c = tx * 4 + j;
-    if (row < n && c < nb) {
-      wpanel[(long)row * NB + c] = acc[j];
-      A[(long)row * n + k0 + c] = N::mul(acc[j], dinv[k0 + c]);
+  __syncthreads();
+  const int c = tid / 4, part = tid % 4;
+  for (int i = 0; i < NB; ++i)
+    if (part == 0) X[i * NB + c] = (i == c && c < nb) ? N::one() : N::zero();
+  __syncwarp();
+  for (int i = 1; i < nb; ++i) {                    // uniform trip count: the shuffles need the whole warp
+    const bool active = c < i;
+    T s = N::zero();
+    if (active)
+      for (int t = c + part; t < i; t += 4) s = N::fma_(S[i * NB + t], X[t * NB + c], s);
+    s = N::add(s, shfl_xor_T(s, 1));
+    s = N::add(s, shfl_xor_T(s, 2));
+    if (active && part == 0) X[i * NB + c] = N::sub(N::zero(), s);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * NB; e += blockDim.x) linv[(long)blockIdx.x * NB * NB + e] = X[e];
+}
+
+// ---- panel: W_i = A_i L_kk^-T (forward substitution), L_i = W_i D^-1 -------------------------------------------
+// One CTA (4 warps) per 32 rows below the diagonal block: all threads stage the rows and the strict lower L_kk in
+// shared memory (coalesced); four lanes share each row, w_c = a_c - sum_{t<c} w_t L_ct with lane q summing
+// t = q mod 4 and two shuffles joining the parts; then all threads write the rows back as W (panel buffer) and L
+// (in A).  Half the FP64 work of multiplying by an explicit inverse, and no inverse on the critical path.
+constexpr int PR = 32;            // rows per CTA
+constexpr int PT = 128;           // threads per CTA
+template <class T>
+__global__ void __launch_bounds__(PT) panel_kernel(T* A, int n, int k0, const T* dinv, T* wpanel) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ls = reinterpret_cast<T*>(smem_raw);           // [NB][SD]: Ls[c][t] = L_kk[c][t], t < c
+  T* Ws = Ls + NB * SD;                              // [NB][PR + 1]: Ws[c][r] = row r, column c
+  using N = Num<T>;
+  const int tid = threadIdx.x;
+  const int r0 = k0 + NB + blockIdx.x * PR;
+  for (int e = tid; e < NB * NB; e += PT) {
+    const int c = e / NB, t = e % NB;
+    Ls[c * SD + t] = t < c ? A[(long)(k0 + c) * n + k0 + t] : N::zero();
+  }
+  for (int e = tid; e < PR * NB; e += PT) {
+    const int rr = e / NB, c = e % NB, row = r0 + rr;
+    Ws[c * (PR + 1) + rr] = row < n ? A[(long)row * n + k0 + c] : N::zero();
+  }
+  __syncthreads();
+  const int r = tid / 4, q = tid % 4;               // row of this lane group, part of the sum
+  for (int c = 1; c < NB; ++c) {
+    T s = N::zero();
+    for (int t = q; t < c; t += 4) s = N::fma_(Ws[t * (PR + 1) + r], Ls[c * SD + t], s);
+    s = N::add(s, shfl_xor_T(s, 1));
+    s = N::add(s, shfl_xor_T(s, 2));
+    if (q == 0) Ws[c * (PR + 1) + r] = N::sub(Ws[c * (PR + 1) + r], s);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (int e = tid; e < PR * NB; e += PT) {
+    const int rr = e / NB, c = e % NB, row = r0 + rr;
+    if (row < n) {
+      const T w = Ws[c * (PR + 1) + rr];
+      wpanel[(long)row * NB + c] = w;
+      A[(long)row * n + k0 + c] = N::mul(w, dinv[k0 + c]);
     }
   }
 }
@@ -465,7 +502,7 @@ size_t ldlt_scratch_elems(int n) {
 // double-buffered because the side stream still reads panel k while panel k+1 is written.
 template <class T>
 static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel,
-                                          cudaStream_t st, size_t dsmem, const OzakiPlan* oz) {
+                                          cudaStream_t st, size_t dsmem, size_t psmem, const OzakiPlan* oz) {
   const int nblk = (n + NB - 1) / NB;
   T* wp[2] = {wpanel, wpanel + (size_t)(nblk + 1) * NB * NB};
   cudaStream_t side = ctx->side_stream;
@@ -477,7 +514,7 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
   }
   {
     ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
-    diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, 0, dinv, linv_blocks, ctx->d_status);
+    diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, 0, dinv, ctx->d_status);
     CDWAC_LAUNCH_CHECK(ctx);
   }
   // Step kb: panel kb (overlaps the side stream's update kb-1), then wait for that update (it touched block
@@ -489,7 +526,7 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
     cdwac_status rc;
     {
       ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
-      panel_kernel<T><<<ceil_div(rest, 16), 256, 0, st>>>(A, n, k0, dinv, linv_blocks, w);
+      panel_kernel<T><<<ceil_div(rest, PR), PT, psmem, st>>>(A, n, k0, dinv, w);
       CDWAC_LAUNCH_CHECK(ctx);
       // digit planes of this step (double-buffered like the panel: the side stream may still read step kb - 1)
       if (oz && (rc = ozaki_slice<T>(ctx, *oz, kb & 1, A, n, k0, w, st))) return rc;
@@ -520,7 +557,7 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
     }
     {
       ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
-      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0 + NB, dinv, linv_blocks, ctx->d_status);
+      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0 + NB, dinv, ctx->d_status);
       CDWAC_LAUNCH_CHECK(ctx);
     }
   }
@@ -534,11 +571,24 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
 
 size_t ldlt_tc_scratch_bytes(int n, bool cplx) { return ozaki_scratch_bytes(n, cplx); }
 
+// Inverses of every diagonal block at once (needed by the solves, not by the factorisation itself).
+template <class T>
+static cdwac_status launch_inverses(cdwac_ctx* ctx, const T* A, int n, T* linv_blocks, size_t ismem, cudaStream_t st) {
+  ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
+  inverse_kernel<T><<<ceil_div(n, NB), 256, ismem, st>>>(A, n, linv_blocks);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
 template <class T>
 cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T* wpanel, cudaStream_t st,
                          void* oz_scratch) {
-  const size_t dsmem = 2 * NB * NB * sizeof(T);
+  const size_t dsmem = (size_t)NB * SD * sizeof(T);
+  const size_t psmem = (size_t)(NB * SD + NB * (PR + 1)) * sizeof(T);
+  const size_t ismem = 2 * (size_t)NB * NB * sizeof(T);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(diag_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsmem));
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem));
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(inverse_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ismem));
   OzakiPlan plan;
   const OzakiPlan* oz = nullptr;
   if (oz_scratch && n > NB) {
@@ -546,12 +596,15 @@ cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T
     if (rc) return rc;
     oz = &plan;
   }
-  if (ctx->side_stream && ctx->ev_panel && ctx->ev_bulk)
-    return ldlt_factor_lookahead<T>(ctx, A, n, dinv, linv_blocks, wpanel, st, dsmem, oz);
+  if (ctx->side_stream && ctx->ev_panel && ctx->ev_bulk) {
+    cdwac_status rc = ldlt_factor_lookahead<T>(ctx, A, n, dinv, linv_blocks, wpanel, st, dsmem, psmem, oz);
+    if (rc) return rc;
+    return launch_inverses<T>(ctx, A, n, linv_blocks, ismem, st);
+  }
   for (int k0 = 0; k0 < n; k0 += NB) {
     {
       ProfScope ps(ctx, PROF_LDLT_DIAG, st, 2);
-      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0, dinv, linv_blocks, ctx->d_status);
+      diag_kernel<T><<<1, 256, dsmem, st>>>(A, n, k0, dinv, ctx->d_status);
       CDWAC_LAUNCH_CHECK(ctx);
     }
     int rest = n - (k0 + NB);
@@ -559,7 +612,7 @@ cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T
     int rblk = ceil_div(rest, 64);
     {
       ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
-      panel_kernel<T><<<ceil_div(rest, 16), 256, 0, st>>>(A, n, k0, dinv, linv_blocks, wpanel);
+      panel_kernel<T><<<ceil_div(rest, PR), PT, psmem, st>>>(A, n, k0, dinv, wpanel);
       CDWAC_LAUNCH_CHECK(ctx);
     }
     ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
@@ -572,7 +625,7 @@ cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T
       CDWAC_LAUNCH_CHECK(ctx);
     }
   }
-  return CDWAC_OK;
+  return launch_inverses<T>(ctx, A, n, linv_blocks, ismem, st);
 }
 
 template <class T>
