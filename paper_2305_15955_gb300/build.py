@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcdwac.so")
 
-SOURCES = ["api.cu", "grid.cu", "pi_simt.cu", "ldlt.cu", "thiele.cu", "sigma.cu", "tc_pi.cu", "noalloc.cu", "wsolve32.cu", "batch.cu", "mlp.cu", "ozaki.cu", "wsolve_tc.cu"]
+SOURCES = ["api.cu", "grid.cu", "pi_simt.cu", "ldlt.cu", "thiele.cu", "sigma.cu", "tc_pi.cu", "noalloc.cu", "batch.cu", "mlp.cu", "ozaki.cu", "wsolve_tc.cu"]
 # thiele.cu and grid.cu round every product and sum as written (no FMA contraction): the greedy decisions and
 # the double-double grid arithmetic depend on it
 EXTRA = {"thiele.cu": ["--fmad=false"], "grid.cu": ["--fmad=false"]}

@@ -465,7 +465,7 @@ static size_t real_lane_bytes(const cdwac_system* sys, bool mixed) {
   const int n = sys->n_aux, ns = sys->n_states, n_occ = sys->n_occ;
   const long n_ov = (long)n_occ * (sys->n_basis - n_occ);
   size_t b = factor_scratch_bytes<cplx>(n, ns * n_occ) + 2048;
-  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns * n_occ) + ldlt_tc_scratch_bytes(n, true) + 768;
+  if (mixed) b += tc_pi_lane_bytes(n, n_ov) + wsolve_tc_c_scratch_bytes(n, ns * n_occ) + ldlt_tc_scratch_bytes(n, true) + 768;
   return b;
 }
 
@@ -475,7 +475,7 @@ static RealBufs carve_real(Arena& ar, const cdwac_system* sys, bool mixed) {
   RealBufs b;
   b.f = carve_factor<cplx>(ar, n, ns * n_occ);
   b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov)) : nullptr;
-  b.wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns * n_occ)) : nullptr;
+  b.wsc = mixed ? ar.take<char>(wsolve_tc_c_scratch_bytes(n, ns * n_occ)) : nullptr;
   b.oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, true)) : nullptr;
   return b;
 }
@@ -501,7 +501,7 @@ static cdwac_status real_points(cdwac_ctx* lc, const cdwac_system* sys, const cd
     }
     ProfScope ps(lc, PROF_QUADFORM, st);
     if (mixed)
-      rc = wsolve_c32(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
+      rc = wsolve_tc_c(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
                       Wr + (long)j * n_occ, (long)nr * n_occ, b.wsc, st);
     else
       rc = ldlt_quadform<cplx>(lc, b.f.A, b.f.dinv, b.f.linv, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, ns, n_occ,
@@ -593,7 +593,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   const int ns = sys->n_states;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
   size_t bytes = n_ov * sizeof(double) + factor_scratch_bytes<cplx>(n, ns) + sizeof(cplx) * (ns + 2) + 2048;
-  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_c32_scratch_bytes(n, ns) + ldlt_tc_scratch_bytes(n, true) + 512;
+  if (mixed) bytes += tc_pi_scratch_bytes(n, n_ov) + wsolve_tc_c_scratch_bytes(n, ns) + ldlt_tc_scratch_bytes(n, true) + 512;
   cdwac_status rc = ensure_scratch(ctx, bytes);
   if (rc) return rc;
   Arena ar(ctx->scratch);
@@ -602,7 +602,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
   cplx* zdev = ar.take<cplx>(1);
   cplx* Wv = ar.take<cplx>(ns);
   void* tcs = mixed ? ar.take<char>(tc_pi_scratch_bytes(n, n_ov)) : nullptr;
-  void* wsc = mixed ? ar.take<char>(wsolve_c32_scratch_bytes(n, ns)) : nullptr;
+  void* wsc = mixed ? ar.take<char>(wsolve_tc_c_scratch_bytes(n, ns)) : nullptr;
   void* oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, true)) : nullptr;
   if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
   if (mixed && (rc = tc_pi_prepare(ctx, sys->O_ia, sys->O_dtype, n, n_ov, tcs, st))) return rc;
@@ -625,7 +625,7 @@ static cdwac_status plain_cd_residues(cdwac_ctx* ctx, const cdwac_system* sys, c
       const void* Om = sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + m)
                                                  : (const void*)((const float*)sys->O_n + m);
       if (mixed)
-        rc = wsolve_c32(ctx, f.A, f.dinv, f.linv, n, Om, sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1, wsc, st);
+        rc = wsolve_tc_c(ctx, f.A, f.dinv, f.linv, n, Om, sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1, wsc, st);
       else
         rc = ldlt_quadform<cplx>(ctx, f.A, f.dinv, f.linv, n, Om, sys->O_dtype, (long)n * nb, nb, ns, 1, Wv, 1,
                                  f.ywork, st);

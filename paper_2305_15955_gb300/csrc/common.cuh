@@ -252,16 +252,12 @@ size_t wsolve_tc_scratch_bytes(int n, int n_cols);
 cdwac_status wsolve_tc(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
                        int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,
                        int cols_per_state, double* W_out, long w_state_stride, void* scratch, cudaStream_t st);
-// wsolve32.cu: the same W on the CUDA cores (y = L^-1 o, u = L^-1 Pi o in FP32)
-size_t wsolve32_scratch_bytes(int n, int n_cols);
-cdwac_status wsolve32(cdwac_ctx* ctx, const double* L, const double* dinv, const double* linv, const float* negpi32,
-                      int n, const void* O, int dtype, long o_state_stride, long ld_o, int n_states,
-                      int cols_per_state, double* W_out, long w_state_stride, void* scratch, cudaStream_t st);
-// complex symmetric case (near-real points, residues), mixed path: W = sum y^2 / d - sum o^2 in FP32 complex
-size_t wsolve_c32_scratch_bytes(int n, int n_cols);
-cdwac_status wsolve_c32(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const cplx* linv, int n, const void* O,
-                        int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, cplx* W_out,
-                        long w_state_stride, void* scratch, cudaStream_t st);
+// wsolve_tc.cu, near-real points and residues: W = sum_P y_P^2 / d_P - sum_P o_P^2, y = L^-1 o (complex symmetric
+// FP64 factor), blocked forward substitution with tensor-core updates
+size_t wsolve_tc_c_scratch_bytes(int n, int n_cols);
+cdwac_status wsolve_tc_c(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const cplx* linv, int n, const void* O,
+                         int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, cplx* W_out,
+                         long w_state_stride, void* scratch, cudaStream_t st);
 // thiele.cu
 cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_imag, int n_real, const double* xi,
                                const double* W_imag, int n_basis, const double* z_real, const double* W_real,

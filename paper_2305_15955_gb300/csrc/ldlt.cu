@@ -64,8 +64,9 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
   using N = Num<T>;
   const int nb = min(NB, n - k0);
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
+#pragma unroll
+  for (int it = 0; it < NB * NB / 256; ++it) {   // fixed count: every load of the block in flight at once
+    const int e = tid + 256 * it, i = e / NB, j = e % NB;
     S[i * SD + j] = (i < nb && j <= i) ? A[(long)(k0 + i) * n + (k0 + j)] : (i == j ? N::one() : N::zero());
   }
   // this thread's trailing-triangle elements: number e -> (i, k), u = 63 - k, e in [u(u+1)/2, u(u+1)/2 + u]
@@ -125,8 +126,9 @@ __global__ void __launch_bounds__(256) inverse_kernel(const T* A, int n, T* linv
   using N = Num<T>;
   const int k0 = blockIdx.x * NB, nb = min(NB, n - k0);
   const int tid = threadIdx.x;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, j = e % NB;
+#pragma unroll
+  for (int it = 0; it < NB * NB / 256; ++it) {
+    const int e = tid + 256 * it, i = e / NB, j = e % NB;
     S[e] = (i < nb && j < i) ? A[(long)(k0 + i) * n + (k0 + j)] : N::zero();
   }
   __syncthreads();
@@ -163,12 +165,14 @@ __global__ void __launch_bounds__(PT) panel_kernel(T* A, int n, int k0, const T*
   using N = Num<T>;
   const int tid = threadIdx.x;
   const int r0 = k0 + NB + blockIdx.x * PR;
-  for (int e = tid; e < NB * NB; e += PT) {
-    const int c = e / NB, t = e % NB;
+#pragma unroll 16
+  for (int it = 0; it < NB * NB / PT; ++it) {     // fixed counts: the loads are issued back to back
+    const int e = tid + PT * it, c = e / NB, t = e % NB;
     Ls[c * SD + t] = t < c ? A[(long)(k0 + c) * n + k0 + t] : N::zero();
   }
-  for (int e = tid; e < PR * NB; e += PT) {
-    const int rr = e / NB, c = e % NB, row = r0 + rr;
+#pragma unroll
+  for (int it = 0; it < PR * NB / PT; ++it) {
+    const int e = tid + PT * it, rr = e / NB, c = e % NB, row = r0 + rr;
     Ws[c * (PR + 1) + rr] = row < n ? A[(long)row * n + k0 + c] : N::zero();
   }
   __syncthreads();
@@ -182,8 +186,9 @@ __global__ void __launch_bounds__(PT) panel_kernel(T* A, int n, int k0, const T*
     __syncwarp();
   }
   __syncthreads();
-  for (int e = tid; e < PR * NB; e += PT) {
-    const int rr = e / NB, c = e % NB, row = r0 + rr;
+#pragma unroll
+  for (int it = 0; it < PR * NB / PT; ++it) {
+    const int e = tid + PT * it, rr = e / NB, c = e % NB, row = r0 + rr;
     if (row < n) {
       const T w = Ws[c * (PR + 1) + rr];
       wpanel[(long)row * NB + c] = w;

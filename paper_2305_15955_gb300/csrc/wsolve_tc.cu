@@ -9,6 +9,11 @@
 //   for b:  Y_b = L_bb^-1 T_b                   CUDA cores, FP32 (64 x 64 times 64 x 2C), W partial sums in FP64
 //           T_>b -= L_>b,b Y_b                  split-BF16 tensor-core GEMM with K = 64
 //
+// Near the real axis (complex symmetric L, real o) the same blocked substitution gives y = L^-1 o and
+// W_nm = sum_P y_P^2 / d_P - sum_P o_P^2 (W is O(1) there: no cancellation).  The complex update is one real GEMM
+// with K = 128 per block: A = [Re L | -Im L], and the rows of B are [Re y | Im y] for the real parts of T and
+// [Im y | -Re y] for the imaginary parts.
+//
 // T is held column-major (T[col][row], col < 2C) so that both the GEMM epilogue (a warp writes 32 consecutive rows
 // of one column) and the block solve (64 consecutive rows of a column) touch contiguous memory.  The BF16 planes of
 // the factor, of Pi and of O^T are K-major for TMA (128-byte swizzle); the planes of Y_b are [2C][64].  The
@@ -135,15 +140,19 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
       tmem_ld32(tmem + lane_base + c0, v);
       if (row < M) {
         float* o = out + row_off + row;
+        // every load of the chunk before any store: the compiler cannot prove o[j ld] and o[k ld] distinct
+        float cur[32];
+        if (SUB) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = tn * BN + c0 + j;
+            cur[j] = col < N ? o[(long)col * ld] : 0.f;
+          }
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int col = tn * BN + c0 + j;
-          if (col < N) {
-            if (SUB)
-              o[(long)col * ld] -= __uint_as_float(v[j]);
-            else
-              o[(long)col * ld] = __uint_as_float(v[j]);
-          }
+          if (col < N) o[(long)col * ld] = SUB ? cur[j] - __uint_as_float(v[j]) : __uint_as_float(v[j]);
         }
       }
     }
@@ -190,7 +199,8 @@ __global__ void pi_split_kernel(const float* __restrict__ negpi, int n, int npad
   }
 }
 
-// O^T: column c = (state s, orbital m) -> FP32 row T[c][0..n) (zero padded to npad) and its BF16 hi/lo planes
+// O^T: column c = (state s, orbital m) -> FP32 row T[c][0..n) (zero padded to npad) and, if oh is given, its
+// BF16 hi/lo planes
 template <class TIn>
 __global__ void o_transpose_kernel(const TIn* __restrict__ O, long o_state_stride, long ld_o, int cols_per_state,
                                    int n_cols, int n, int npad, float* __restrict__ t32, __nv_bfloat16* __restrict__ oh,
@@ -214,7 +224,7 @@ __global__ void o_transpose_kernel(const TIn* __restrict__ O, long o_state_strid
       const float v = tile[tx][k];
       const long e = (long)c * npad + P;
       t32[e] = v;
-      split_bf16(v, oh[e], ol[e]);
+      if (oh) split_bf16(v, oh[e], ol[e]);
     }
   }
 }
@@ -236,9 +246,14 @@ __global__ void __launch_bounds__(256) block_solve_kernel(const float* __restric
   const int tid = threadIdx.x, r = tid % 64, g = tid / 64;
   const int r0 = b * 64;
   const float* X = linv32 + (long)b * 64 * 64;
-  for (int e = tid; e < 64 * 64; e += 256) Xs[e / 64][e % 64] = X[e];
-  for (int e = tid; e < 2 * SP * 64; e += 256) {
-    const int cc = e / 64, k = e % 64;
+#pragma unroll
+  for (int it = 0; it < 64 * 64 / 256; ++it) {
+    const int e = tid + 256 * it;
+    Xs[e / 64][e % 64] = X[e];
+  }
+#pragma unroll
+  for (int it = 0; it < 2 * SP * 64 / 256; ++it) {
+    const int e = tid + 256 * it, cc = e / 64, k = e % 64;
     const int col = cc < SP ? m0 + cc : C + m0 + (cc - SP);
     const bool ok = (cc < SP ? m0 + cc : m0 + cc - SP) < C && r0 + k < n;
     Ts[cc][k] = ok ? T[(long)col * ld + r0 + k] : 0.f;
@@ -288,6 +303,132 @@ __global__ void w_reduce_kernel(const double* __restrict__ part, int nblk, int C
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += part[(long)b * C + c];
   W_out[(long)(c / cols_per_state) * w_state_stride + c % cols_per_state] = s;
+}
+
+// ---- near-real (complex symmetric) solve ---------------------------------------------------------------------
+
+struct f2 {
+  float x, y;
+};
+
+// Strict lower complex factor -> BF16 hi/lo planes [n][2 npad]: block b occupies columns 128b..128b+127 as
+// [Re L(:, 64b..64b+63) | -Im L(:, 64b..64b+63)]; complex diagonal-block inverses -> FP32 pairs.
+__global__ void cfactor_split_kernel(const cplx* __restrict__ L, int n, int npad, const cplx* __restrict__ linv,
+                                     int nblk, __nv_bfloat16* __restrict__ lh, __nv_bfloat16* __restrict__ ll,
+                                     f2* __restrict__ linv32) {
+  const long w2 = 2L * npad, total = (long)n * w2, tl = (long)nblk * 64 * 64;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total + tl; e += (long)gridDim.x * blockDim.x) {
+    if (e < total) {
+      const long r = e / w2, cc = e % w2;
+      const long b = cc / 128, k = cc % 128, col = 64 * b + (k % 64);
+      float v = 0.f;
+      if (col < r) {
+        const cplx x = L[r * n + col];
+        v = k < 64 ? (float)x.x : (float)-x.y;
+      }
+      split_bf16(v, lh[e], ll[e]);
+    } else {
+      const cplx x = linv[e - total];
+      linv32[e - total] = f2{(float)x.x, (float)x.y};
+    }
+  }
+}
+
+// Block step b, complex: Y_b = X_b T_b (T rows c = Re, C + c = Im), planes [2C][128] for the update
+// (row c: [Re y | Im y], row C + c: [Im y | -Re y]) and part[b][c] = sum_r y_r^2 / d_r (complex, FP64).
+// One CTA per 8 columns; thread (r, g) owns row r of columns 2g and 2g + 1.
+constexpr int SPC = 8;
+__global__ void __launch_bounds__(256) block_solve_c_kernel(const float* __restrict__ T, long ld, int n, int C, int b,
+                                                            const f2* __restrict__ linv32,
+                                                            const cplx* __restrict__ dinv,
+                                                            __nv_bfloat16* __restrict__ yh,
+                                                            __nv_bfloat16* __restrict__ yl,
+                                                            double* __restrict__ part) {
+  __shared__ f2 Xs[64][65];
+  __shared__ float Tr[SPC][65], Ti[SPC][65];
+  __shared__ double red[4][64][2][2];
+  const int m0 = blockIdx.x * SPC;
+  const int tid = threadIdx.x, r = tid % 64, g = tid / 64;
+  const int r0 = b * 64;
+  const f2* X = linv32 + (long)b * 64 * 64;
+#pragma unroll
+  for (int it = 0; it < 64 * 64 / 256; ++it) {
+    const int e = tid + 256 * it;
+    Xs[e / 64][e % 64] = X[e];
+  }
+#pragma unroll
+  for (int it = 0; it < 2 * SPC * 64 / 256; ++it) {
+    const int e = tid + 256 * it, cc = e / 64, k = e % 64;
+    const int m = m0 + (cc % SPC);
+    const bool ok = m < C && r0 + k < n;
+    const float v = ok ? T[(long)(cc < SPC ? m : C + m) * ld + r0 + k] : 0.f;
+    if (cc < SPC)
+      Tr[cc][k] = v;
+    else
+      Ti[cc - SPC][k] = v;
+  }
+  __syncthreads();
+  float yr[2] = {0.f, 0.f}, yi[2] = {0.f, 0.f};
+  for (int k = 0; k <= r; ++k) {
+    const f2 x = Xs[r][k];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float tr = Tr[2 * g + j][k], ti = Ti[2 * g + j][k];
+      yr[j] = fmaf(x.x, tr, fmaf(-x.y, ti, yr[j]));
+      yi[j] = fmaf(x.x, ti, fmaf(x.y, tr, yi[j]));
+    }
+  }
+  const int row = r0 + r;
+  const cplx di = row < n ? dinv[row] : mkc(0.0, 0.0);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int m = m0 + 2 * g + j;
+    const double a = yr[j], bb = yi[j];
+    const double sr = a * a - bb * bb, si = 2.0 * a * bb;   // y^2
+    red[g][r][j][0] = sr * di.x - si * di.y;
+    red[g][r][j][1] = sr * di.y + si * di.x;
+    if (m < C) {
+      __nv_bfloat16 h, l;
+      split_bf16(yr[j], h, l);
+      yh[(long)m * 128 + r] = h;
+      yl[(long)m * 128 + r] = l;
+      split_bf16(yi[j], h, l);
+      yh[(long)m * 128 + 64 + r] = h;
+      yl[(long)m * 128 + 64 + r] = l;
+      yh[(long)(C + m) * 128 + r] = h;
+      yl[(long)(C + m) * 128 + r] = l;
+      split_bf16(-yr[j], h, l);
+      yh[(long)(C + m) * 128 + 64 + r] = h;
+      yl[(long)(C + m) * 128 + 64 + r] = l;
+    }
+  }
+  __syncthreads();
+  if (tid < 2 * SPC) {
+    const int mm = tid / 2, part_ri = tid % 2, gg = mm / 2, j = mm % 2, m = m0 + mm;
+    double acc = 0.0;
+    for (int k = 0; k < 64; ++k) acc += red[gg][k][j][part_ri];
+    if (m < C) part[((long)b * C + m) * 2 + part_ri] = acc;
+  }
+}
+
+// W[c] = sum_b part[b][c] - sum_P o_P^2 for column c = (s, m), written to W_out[s * w_state_stride + m]
+template <class TIn>
+__global__ void w_reduce_c_kernel(const double* __restrict__ part, int nblk, int C, int n, const TIn* __restrict__ O,
+                                  long o_state_stride, long ld_o, int cols_per_state, cplx* __restrict__ W_out,
+                                  long w_state_stride) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  const int s = c / cols_per_state, m = c % cols_per_state;
+  double re = 0.0, im = 0.0, oo = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    re += part[((long)b * C + c) * 2];
+    im += part[((long)b * C + c) * 2 + 1];
+  }
+  for (int P = 0; P < n; ++P) {
+    const double o = (double)O[s * o_state_stride + (long)P * ld_o + m];
+    oo += o * o;
+  }
+  W_out[(long)s * w_state_stride + m] = mkc(re - oo, im);
 }
 
 bool make_map(CUtensorMap* m, const void* base, int rows, long kpad) {
@@ -347,6 +488,83 @@ cdwac_status gemm(cdwac_ctx* ctx, const GemmMaps& maps, int M, int N, int k_tile
 }
 
 }  // namespace
+
+namespace {
+struct CBufs {
+  __nv_bfloat16 *lh, *ll, *yh, *yl;
+  float* t;
+  f2* linv32;
+  double* part;
+  int npad, nblk;
+};
+
+CBufs carve_c(void* scratch, int n, int C) {
+  CBufs b;
+  b.npad = ((n + 63) / 64) * 64;
+  b.nblk = (n + 63) / 64;
+  Arena ar(scratch);
+  const size_t sq = (size_t)n * 2 * b.npad;
+  b.lh = ar.take<__nv_bfloat16>(sq);
+  b.ll = ar.take<__nv_bfloat16>(sq);
+  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 128);
+  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 128);
+  b.t = ar.take<float>((size_t)2 * C * b.npad);
+  b.linv32 = ar.take<f2>((size_t)b.nblk * 64 * 64);
+  b.part = ar.take<double>((size_t)b.nblk * C * 2);
+  return b;
+}
+}  // namespace
+
+size_t wsolve_tc_c_scratch_bytes(int n, int n_cols) {
+  const size_t npad = ((size_t)n + 63) / 64 * 64, nblk = npad / 64;
+  return 2 * ((size_t)n * 2 * npad * 2 + 256) + 2 * ((size_t)2 * n_cols * 128 * 2 + 256) +
+         ((size_t)2 * n_cols * npad * 4 + 256) + (nblk * 64 * 64 * 8 + 256) + (nblk * n_cols * 16 + 256) + 1024;
+}
+
+cdwac_status wsolve_tc_c(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const cplx* linv, int n, const void* O,
+                         int dtype, long o_state_stride, long ld_o, int n_states, int cols_per_state, cplx* W_out,
+                         long w_state_stride, void* scratch, cudaStream_t st) {
+  const int C = n_states * cols_per_state;
+  if (C <= 0) return CDWAC_OK;
+  CBufs b = carve_c(scratch, n, C);
+  const long ld = b.npad;
+  {
+    const long work = (long)n * 2 * b.npad + (long)b.nblk * 4096;
+    cfactor_split_kernel<<<grid_of(ctx, work), 256, 0, st>>>(L, n, b.npad, linv, b.nblk, b.lh, b.ll, b.linv32);
+    CDWAC_LAUNCH_CHECK(ctx);
+    dim3 tg((b.npad + 31) / 32, (C + 31) / 32);
+    if (dtype == CDWAC_F64)
+      o_transpose_kernel<double><<<tg, 256, 0, st>>>((const double*)O, o_state_stride, ld_o, cols_per_state, C, n,
+                                                     b.npad, b.t, nullptr, nullptr);
+    else
+      o_transpose_kernel<float><<<tg, 256, 0, st>>>((const float*)O, o_state_stride, ld_o, cols_per_state, C, n,
+                                                    b.npad, b.t, nullptr, nullptr);
+    CDWAC_LAUNCH_CHECK(ctx);
+    CDWAC_CUDA_TRY(ctx, cudaMemsetAsync(b.t + (long)C * ld, 0, sizeof(float) * (size_t)C * ld, st));
+  }
+  GemmMaps upd;
+  if (!make_map(&upd.ah, b.lh, n, 2L * b.npad) || !make_map(&upd.al, b.ll, n, 2L * b.npad) ||
+      !make_map(&upd.bh, b.yh, 2 * C, 128) || !make_map(&upd.bl, b.yl, 2 * C, 128))
+    return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the complex W solve (n=%d, C=%d)", n, C);
+  cdwac_status rc;
+  for (int blk = 0; blk < b.nblk; ++blk) {
+    block_solve_c_kernel<<<(C + SPC - 1) / SPC, 256, 0, st>>>(b.t, ld, n, C, blk, b.linv32, dinv, b.yh, b.yl,
+                                                               b.part);
+    CDWAC_LAUNCH_CHECK(ctx);
+    const int r1 = (blk + 1) * 64;
+    if (r1 < n && (rc = gemm<true>(ctx, upd, n - r1, 2 * C, 2, blk * 128, r1, b.t, ld, r1, st))) return rc;
+  }
+  if (dtype == CDWAC_F64)
+    w_reduce_c_kernel<double><<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, n, (const double*)O,
+                                                               o_state_stride, ld_o, cols_per_state, W_out,
+                                                               w_state_stride);
+  else
+    w_reduce_c_kernel<float><<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, n, (const float*)O,
+                                                              o_state_stride, ld_o, cols_per_state, W_out,
+                                                              w_state_stride);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
 
 size_t wsolve_tc_scratch_bytes(int n, int n_cols) {
   const size_t npad = ((size_t)n + 63) / 64 * 64, nblk = npad / 64;
