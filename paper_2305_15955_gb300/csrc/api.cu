@@ -445,10 +445,13 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
     return imag_freqs(ctx, sys, prm, xi, W_imag, D, tc_shared, b, 0, 1, st);
   }
   if ((rc = fork_lanes(ctx, L, st))) return rc;
-  for (int l = 0; l < L; ++l) {
+  // frequencies are enqueued round robin over the lanes: the host's launch queue is bounded, so enqueueing one
+  // lane's whole share first would let it drain alone before the next lane's work even arrives
+  for (int k = 0; k < prm->n_imag; ++k) {
+    const int l = k % L;
     Arena al(ctx->lanes[l]->scratch);
     ImagBufs b = carve_imag(al, sys, mixed);
-    rc = imag_freqs(ctx->lanes[l], sys, prm, xi, W_imag, D, tc_shared, b, l, L, ctx->lane_streams[l]);
+    rc = imag_freqs(ctx->lanes[l], sys, prm, xi, W_imag, D, tc_shared, b, k, prm->n_imag, ctx->lane_streams[l]);
     if (rc) return set_error(ctx, rc, "lane %d: %s", l, ctx->lanes[l]->last_error.c_str());
   }
   return join_lanes(ctx, L, st);
@@ -557,10 +560,11 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
       if ((rc = real_points(ctx, sys, prm, zr, Wr, D, tc_shared, b, 0, 1, st))) return rc;
     } else {
       if ((rc = fork_lanes(ctx, L, st))) return rc;
-      for (int l = 0; l < L; ++l) {
+      for (int j = 0; j < nr; ++j) {   // round robin over the lanes, as for the imaginary axis
+        const int l = j % L;
         Arena al(ctx->lanes[l]->scratch);
         RealBufs b = carve_real(al, sys, mixed);
-        rc = real_points(ctx->lanes[l], sys, prm, zr, Wr, D, tc_shared, b, l, L, ctx->lane_streams[l]);
+        rc = real_points(ctx->lanes[l], sys, prm, zr, Wr, D, tc_shared, b, j, nr, ctx->lane_streams[l]);
         if (rc) return set_error(ctx, rc, "lane %d: %s", l, ctx->lanes[l]->last_error.c_str());
       }
       if ((rc = join_lanes(ctx, L, st))) return rc;
