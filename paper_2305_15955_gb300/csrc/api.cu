@@ -53,7 +53,7 @@ bool create_factor_streams(cdwac_ctx* ctx) {
       cudaEventCreateWithFlags(&ctx->ev_crit_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_crit_out, cudaEventDisableTiming) != cudaSuccess)
     return false;
-  ctx->side_stream = ctx->own_side;
+  ctx->side_stream = ctx->lookahead ? ctx->own_side : nullptr;
   return true;
 }
 
@@ -80,6 +80,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
   }
   ctx->num_sms = p.multiProcessorCount;
   if (const char* fl = getenv("CDWAC_FREQ_LANES")) ctx->freq_lanes = std::max(1, std::min(16, atoi(fl)));
+  if (const char* la = getenv("CDWAC_LOOKAHEAD")) ctx->lookahead = atoi(la) != 0;
   if (!create_factor_streams(ctx)) {
     cdwac_destroy(ctx);
     return CDWAC_ERR_CUDA;
@@ -322,7 +323,7 @@ static cdwac_status fork_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
   CDWAC_CUDA_TRY(ctx, cudaEventRecord(ctx->ev_fork, st));
   for (int l = 0; l < L; ++l) {
     ctx->lanes[l]->prof = ctx->prof;
-    ctx->lanes[l]->side_stream = ctx->lanes[l]->own_side;
+    ctx->lanes[l]->side_stream = ctx->lookahead ? ctx->lanes[l]->own_side : nullptr;
     CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->lane_streams[l], ctx->ev_fork, 0));
   }
   return CDWAC_OK;

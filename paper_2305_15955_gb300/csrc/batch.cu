@@ -37,6 +37,7 @@ cdwac_status make_lane(cdwac_ctx* parent, cdwac_ctx** out) {
   l->num_sms = parent->num_sms;
   l->d_status = parent->d_status;
   l->h_status = parent->h_status;
+  l->lookahead = parent->lookahead;
   if (!create_factor_streams(l)) {
     cdwac_destroy(l);
     return set_error(parent, CDWAC_ERR_CUDA, "lane creation failed");

@@ -67,6 +67,7 @@ struct cdwac_ctx {
   // batched launch: lane contexts (own scratch and streams, shared status word), fork/join events, graph cache
   bool is_lane = false;
   int freq_lanes = 8;                   // concurrent frequency chains in the W builds (lanes never nest)
+  bool lookahead = true;                // LDL^T bulk updates on the side stream (else one stream, no events)
   std::vector<cdwac_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;
   std::vector<cudaEvent_t> lane_events;
