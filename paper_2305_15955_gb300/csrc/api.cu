@@ -97,7 +97,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
 }
 
 static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",   "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
-                                              "ldlt_fp64", "w_solves",  "thiele_fit", "sigma",         "qp_solve",
+                                              "ldlt",      "w_solves",  "thiele_fit", "sigma",         "qp_solve",
                                               "mlp",       "ldlt_diag", "ldlt_panel", "ldlt_update"};
 
 void cdwac_profile_enable(cdwac_ctx* ctx, int on) {

@@ -411,24 +411,36 @@ __global__ void __launch_bounds__(256) block_solve_c_kernel(const float* __restr
   }
 }
 
-// W[c] = sum_b part[b][c] - sum_P o_P^2 for column c = (s, m), written to W_out[s * w_state_stride + m]
+// W[c] = sum_b part[b][c] - sum_P o_P^2 for column c = (s, m), written to W_out[s * w_state_stride + m]; one
+// CTA per column, the sums over P and b split across its threads
 template <class TIn>
-__global__ void w_reduce_c_kernel(const double* __restrict__ part, int nblk, int C, int n, const TIn* __restrict__ O,
-                                  long o_state_stride, long ld_o, int cols_per_state, cplx* __restrict__ W_out,
-                                  long w_state_stride) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
+__global__ void __launch_bounds__(256) w_reduce_c_kernel(const double* __restrict__ part, int nblk, int C, int n,
+                                                         const TIn* __restrict__ O, long o_state_stride, long ld_o,
+                                                         int cols_per_state, cplx* __restrict__ W_out,
+                                                         long w_state_stride) {
+  __shared__ double sre[256], sim[256];
+  const int c = blockIdx.x, tid = threadIdx.x;
   const int s = c / cols_per_state, m = c % cols_per_state;
-  double re = 0.0, im = 0.0, oo = 0.0;
-  for (int b = 0; b < nblk; ++b) {
+  double re = 0.0, im = 0.0;
+  for (int P = tid; P < n; P += 256) {
+    const double o = (double)O[s * o_state_stride + (long)P * ld_o + m];
+    re -= o * o;
+  }
+  for (int b = tid; b < nblk; b += 256) {
     re += part[((long)b * C + c) * 2];
     im += part[((long)b * C + c) * 2 + 1];
   }
-  for (int P = 0; P < n; ++P) {
-    const double o = (double)O[s * o_state_stride + (long)P * ld_o + m];
-    oo += o * o;
+  sre[tid] = re;
+  sim[tid] = im;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if (tid < h) {
+      sre[tid] += sre[tid + h];
+      sim[tid] += sim[tid + h];
+    }
+    __syncthreads();
   }
-  W_out[(long)s * w_state_stride + m] = mkc(re - oo, im);
+  if (tid == 0) W_out[(long)s * w_state_stride + m] = mkc(sre[0], sim[0]);
 }
 
 bool make_map(CUtensorMap* m, const void* base, int rows, long kpad) {
@@ -555,11 +567,11 @@ cdwac_status wsolve_tc_c(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const 
     if (r1 < n && (rc = gemm<true>(ctx, upd, n - r1, 2 * C, 2, blk * 128, r1, b.t, ld, r1, st))) return rc;
   }
   if (dtype == CDWAC_F64)
-    w_reduce_c_kernel<double><<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, n, (const double*)O,
+    w_reduce_c_kernel<double><<<C, 256, 0, st>>>(b.part, b.nblk, C, n, (const double*)O,
                                                                o_state_stride, ld_o, cols_per_state, W_out,
                                                                w_state_stride);
   else
-    w_reduce_c_kernel<float><<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, n, (const float*)O,
+    w_reduce_c_kernel<float><<<C, 256, 0, st>>>(b.part, b.nblk, C, n, (const float*)O,
                                                               o_state_stride, ld_o, cols_per_state, W_out,
                                                               w_state_stride);
   CDWAC_LAUNCH_CHECK(ctx);
