@@ -23,8 +23,9 @@
 // of Wi and issues Re += -(Wi Li) (negated-A instruction descriptor) and Im += Wi Lr.
 //
 // One CTA per 128 x BN tile of the trailing lower triangle (BN = 64 real, 32 complex): one elected thread issues
-// TMA (3-D maps over the digit planes, 128-byte swizzle), one issues the MMAs, all four warps drain tensor memory
-// (tcgen05.ld 32x32b), stage the FP64 result in shared memory and update A with coalesced row segments.  Every
+// TMA (3-D maps over the digit planes, 128-byte swizzle), one issues the MMAs, all warps drain tensor memory
+// (tcgen05.ld 32x32b; eight warps, two per lane quarter), stage the FP64 result in shared memory and update A with
+// coalesced row segments.  Every
 // mbarrier wait is bounded; on expiry the kernel records CDWAC_ERR_TIMEOUT, waits for the copies it issued and
 // frees its tensor memory.
 #include <cuda.h>
@@ -67,7 +68,7 @@ struct OzMaps {
 };
 
 template <bool CPLX>
-__global__ void __launch_bounds__(128, 1) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
+__global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
                                                            int k1, const int* __restrict__ ew,
                                                            const int* __restrict__ el, int part, unsigned* status) {
   using C = OzCfg<CPLX>;
@@ -176,84 +177,89 @@ __global__ void __launch_bounds__(128, 1) oz_update_kernel(const __grid_constant
 
   const bool done_ok = mbar_wait(&bar_done, 0, nullptr);
   tc_fence_after();
-  __syncthreads();
-  const bool good = done_ok && !abort_flag;
+  // CTA-uniform verdict (the epilogue below has block-wide barriers)
+  const bool good = __syncthreads_and(done_ok ? 1 : 0) && !abort_flag;
   if (threadIdx.x == 0 && !good) {
     raise_status(status, DEV_ERR_TIMEOUT);
     if (loads_issued & 1) mbar_wait(&bar_a0, 0, nullptr);   // no copy may land after the CTA exits
     if (loads_issued & 2) mbar_wait(&bar_a1, 0, nullptr);
   }
   if (good) {
-    // every MMA has completed, so the operand buffers are free: stage [part][warp][32 rows][33] doubles.
-    // Warp w owns tile rows 32w..32w+31; in the read-modify-write lane = column, so each row segment is one
-    // coalesced access.  The A values are fetched in two halves of 16 rows: the first before the tensor-memory
-    // drain (its latency hides behind the integer recombination), the second before the first is written back.
+    // Every MMA has completed, so the operand buffers are free for staging: slot [unit][quarter][32 rows][33].
+    // Warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. tile rows of quarter q = w % 4; the two warpgroups
+    // g = w / 4 take one unit each: column chunk g (real, 64 columns) or part g = re, im (complex, 32 columns).
+    // In the read-modify-write lane = column, so each row segment is one coalesced access; the A values are
+    // fetched before the tensor-memory drain so that their latency hides behind the integer recombination.
     using T = typename std::conditional<CPLX, cplx, double>::type;
     T* Ab = reinterpret_cast<T*>(A_out);
     double* stage = reinterpret_cast<double*>(smem);
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    const int rbase = row0 + warp * 32;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      const int col = col0 + c0 + lane;
-      T cv0[16], cv1[16];
+    const int wq = warp & 3, wg = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    const int c0 = CPLX ? 0 : 32 * wg;                 // column chunk of this warpgroup
+    const int pp = CPLX ? wg : 0;                      // part drained by this warpgroup
+    const int rbase = row0 + wq * 32 + (CPLX ? 16 * wg : 0);   // first row written by this warp
+    const int col = col0 + c0 + lane;
+    T cv0[16], cv1[16];
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr) {
-        const int row = rbase + rr;
-        if (row < n && col <= row) cv0[rr] = Ab[(long)row * n + col];
-      }
-#pragma unroll 1
-      for (int p = 0; p < C::NPART; ++p) {
-        // exact integer recombination N = sum_L acc_L 2^(SH - 7L) on the integer pipe (bits of the lowest levels
-        // below 2^-SH are rounded off, < 2^-60 of the largest term), then one conversion: two FP64 operations per
-        // element in all
-        long long acc[32];
+    for (int rr = 0; rr < 16; ++rr) {
+      const int row = rbase + rr;
+      if (row < n && col <= row) cv0[rr] = Ab[(long)row * n + col];
+    }
+    {
+      // exact integer recombination N = sum_L acc_L 2^(SH - 7L) on the integer pipe (bits of the lowest levels
+      // below 2^-SH are rounded off, < 2^-60 of the largest term), then one conversion: two FP64 operations per
+      // element in all
+      long long acc[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = 0;
+      for (int j = 0; j < 32; ++j) acc[j] = 0;
 #pragma unroll 1
-        for (int idx = 0; idx < S; ++idx) {
-          uint32_t v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(p * C::IM_COL + idx * BN + c0), v);
-          constexpr int SH = C::SHIFT;
-          const int sh = SH - BETA * (idx + 2);
+      for (int idx = 0; idx < S; ++idx) {
+        uint32_t v[32];
+        tmem_ld32(tmem + lane_base + (uint32_t)(pp * C::IM_COL + idx * BN + c0), v);
+        constexpr int SH = C::SHIFT;
+        const int sh = SH - BETA * (idx + 2);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact: an integer < 2^23
-            acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> -sh);   // rounded, not floored
-          }
+        for (int j = 0; j < 32; ++j) {
+          const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact: an integer < 2^23
+          acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> -sh);   // rounded, not floored
         }
-        double* st = stage + ((p * 4 + warp) * 32) * 33;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __ll2double_rn(acc[j]);
       }
+      double* st = stage + ((wg * 4 + wq) * 32) * 33;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __ll2double_rn(acc[j]);
+    }
+    if (CPLX)
+      __syncthreads();   // both parts of every row staged
+    else
       __syncwarp();
+    if (!CPLX) {
 #pragma unroll
       for (int rr = 0; rr < 16; ++rr) {
         const int row = rbase + 16 + rr;
         if (row < n && col <= row) cv1[rr] = Ab[(long)row * n + col];
       }
-      const double sl = scale_l[c0 + lane] * ldexp(1.0, -C::SHIFT);   // exact: powers of two
-      const double* st0 = stage + (warp * 32) * 33;
-      const double* st1 = stage + ((4 + warp) * 32) * 33;
+    }
+    const double sl = scale_l[c0 + lane] * ldexp(1.0, -C::SHIFT);   // exact: powers of two
+    const double* st0 = stage + ((CPLX ? 0 : wg) * 4 + wq) * 32 * 33;
+    const double* st1 = stage + (4 + wq) * 32 * 33;
+    const int r_off = CPLX ? 16 * wg : 0;              // first staged row of this warp within its quarter
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < (CPLX ? 1 : 2); ++h) {
 #pragma unroll
-        for (int rr = 0; rr < 16; ++rr) {
-          const int r = h * 16 + rr, row = rbase + r;
-          if (row < n && col <= row) {
-            const double sc = scale_w[warp * 32 + r] * sl;
-            T v = h == 0 ? cv0[rr] : cv1[rr];
-            if constexpr (!CPLX) {
-              v = fma(-st0[r * 33 + lane], sc, v);
-            } else {
-              v.x = fma(-st0[r * 33 + lane], sc, v.x);
-              v.y = fma(-st1[r * 33 + lane], sc, v.y);
-            }
-            Ab[(long)row * n + col] = v;
+      for (int rr = 0; rr < 16; ++rr) {
+        const int r = r_off + h * 16 + rr, row = row0 + wq * 32 + r;
+        if (row < n && col <= row) {
+          const double sc = scale_w[wq * 32 + r] * sl;
+          T v = h == 0 ? cv0[rr] : cv1[rr];
+          if constexpr (!CPLX) {
+            v = fma(-st0[r * 33 + lane], sc, v);
+          } else {
+            v.x = fma(-st0[r * 33 + lane], sc, v.x);
+            v.y = fma(-st1[r * 33 + lane], sc, v.y);
           }
+          Ab[(long)row * n + col] = v;
         }
       }
-      __syncwarp();
     }
   }
   tc_fence_before();
@@ -387,7 +393,7 @@ cdwac_status ozaki_update(cdwac_ctx* ctx, const OzakiPlan& plan, int buf, T* A, 
   maps.l = plan.lmap[buf];
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(oz_update_kernel<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            C::SMEM));
-  oz_update_kernel<CPLX><<<(unsigned)grid, 128, C::SMEM, st>>>(maps, A, n, k1, plan.ew[buf], plan.el[buf], part,
+  oz_update_kernel<CPLX><<<(unsigned)grid, 256, C::SMEM, st>>>(maps, A, n, k1, plan.ew[buf], plan.el[buf], part,
                                                               ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
