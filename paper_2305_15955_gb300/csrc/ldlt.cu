@@ -37,8 +37,6 @@ __device__ inline cplx shfl_xor_T(cplx v, int m) {
   return mkc(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-__device__ inline bool bad_pivot(double d) { return !(d > 0.0); }
-__device__ inline bool bad_pivot(cplx d) { return !(hypot(d.x, d.y) > 1e-300); }
 __device__ inline unsigned pivot_err(double) { return DEV_ERR_NOT_SPD; }
 __device__ inline unsigned pivot_err(cplx) { return DEV_ERR_SINGULAR; }
 
