@@ -6,17 +6,19 @@
 // 1.2 TFLOP/s and BF16 tensor products at about 2 PFLOP/s, so the update is formed from exact integer slices (the
 // error-free splitting of Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59 (2012) 95-118):
 //
-//   * every row x of W and of L is scaled by 2^-e, e the exponent of its largest magnitude, and cut into S = 8
-//     signed integer digits of 7 bits: x 2^-e = sum_s d_s 2^-7s + r, d_1 in [-128, 128], d_s in [-64, 64] for
-//     s > 1, |r| <= 2^-57.  Each digit is exact in BF16 and each digit product is exact in FP32.
-//   * tcgen05.mma sums, for each level L = s + t (2..9, 36 digit pairs), the products over the panel columns in
+//   * every row x of W and of L is scaled by 2^-e, e the exponent of its largest magnitude, and cut into S signed
+//     integer digits of B bits: x 2^-e = sum_s d_s 2^-Bs + r, |d_1| <= 2^B, |d_s| <= 2^(B-1) for s > 1,
+//     |r| <= 2^-57.  Real: S = 7, B = 8; complex: S = 8, B = 7.  Each digit is exact in BF16 and each digit
+//     product is exact in FP32.
+//   * tcgen05.mma sums, for each level L = s + t (S(S+1)/2 digit pairs), the products over the panel columns in
 //     its own FP32 tensor-memory accumulator.  All partial sums of one level are integers of magnitude below
-//     64 (K) x 40 960 < 2^22 (real) or 2^23 (complex, K = 128), so every accumulation is exact.
-//   * the epilogue forms sum_L 2^-7L acc_L exactly in 64-bit integers (GB300's FP64 units are the scarce
+//     64 x 147 456 < 2^24 (real, largest level) or 128 x 40 960 < 2^23 (complex, K = 128), so every
+//     accumulation is exact.
+//   * the epilogue forms sum_L 2^-BL acc_L exactly in 64-bit integers (GB300's FP64 units are the scarce
 //     resource), converts it once to FP64, scales it by 2^(e_i + e_j) and subtracts it from A (one FMA).
 //
-// The digits dropped (levels above 9 and the remainders r) are below about 2^-54 max|W_i| max|L_j| per column,
-// the size of the rounding error of an FP64 dot product of this length.
+// The digits dropped (levels above S + 1 and the remainders r) are below about 2^-54 max|W_i| max|L_j| per
+// column, the size of the rounding error of an FP64 dot product of this length.
 //
 // Complex symmetric A (no conjugation): Re -= Wr Lr - Wi Li, Im -= Wr Li + Wi Lr.  The CTA loads the digits of
 // Wr with those of Lr and Li, issues Re += Wr Lr and Im += Wr Li, then reloads the operand buffer with the digits
@@ -40,8 +42,6 @@
 namespace {
 using namespace tc;
 
-constexpr int S = 8;        // digits per operand
-constexpr int BETA = 7;     // bits per digit
 constexpr int K = 64;       // panel width (the factorisation's block size)
 constexpr int BM = 128;     // W rows per tile
 constexpr int ROWB = K * 2; // bytes of one digit row: 64 BF16 = one 128-byte swizzle row
@@ -49,6 +49,10 @@ constexpr uint32_t NEG_A = 1u << 13;   // instruction-descriptor bit: negate the
 
 template <bool CPLX>
 struct OzCfg {
+  // digits per operand and bits per digit: real 7 x 8 bits (level sums over K = 64 stay below 9.5e6 < 2^24),
+  // complex 8 x 7 bits (its level sums run over K = 128 products and must stay below 2^24 as well)
+  static constexpr int S = CPLX ? 8 : 7;
+  static constexpr int BETA = CPLX ? 7 : 8;
   static constexpr int NPART = CPLX ? 2 : 1;
   static constexpr int BN = CPLX ? 32 : 64;
   static constexpr int A_TILE = BM * ROWB;          // one digit of 128 W rows (16 KB)
@@ -56,10 +60,10 @@ struct OzCfg {
   static constexpr int A_BYTES = S * A_TILE;        // the digits of one part of W
   static constexpr int B_BYTES = NPART * S * B_TILE;
   static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
-  static constexpr int TMEM_COLS = 512;             // 8 levels x 64 columns, or (re, im) x 8 levels x 32 columns
+  static constexpr int TMEM_COLS = 512;             // 7 levels x 64 columns, or (re, im) x 8 levels x 32 columns
   static constexpr int IM_COL = 256;                // first tensor-memory column of the imaginary accumulators
-  // recombination scale 2^SHIFT: the level-2 sum (|acc_2| <= K 2^14 = 2^20 real, 2^21 complex) times 2^(SHIFT-14)
-  // stays below 2^62, so the int64 sum of all levels cannot overflow
+  // recombination scale 2^SHIFT: the level-2 sum (|acc_2| <= K d_1^2 = 64 * 2^16 real, 128 * 2^14 complex) times
+  // 2^(SHIFT - 2 BETA) stays below 2^63, so the int64 sum of all levels cannot overflow
   static constexpr int SHIFT = CPLX ? 55 : 56;
 };
 
@@ -72,6 +76,7 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
                                                            int k1, const int* __restrict__ ew,
                                                            const int* __restrict__ el, int part, unsigned* status) {
   using C = OzCfg<CPLX>;
+  constexpr int S = C::S, BETA = C::BETA;
   constexpr int BN = C::BN;
   constexpr int Q = K / BN;     // column tiles in the next 64-column block
   constexpr int CT = BM / BN;   // column tiles per 128 rows
@@ -291,6 +296,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const T* __restrict__ A, 
                                                        __nv_bfloat16* __restrict__ lpl, int* __restrict__ ew,
                                                        int* __restrict__ el) {
   constexpr int NPART = sizeof(T) == sizeof(cplx) ? 2 : 1;
+  constexpr int S = OzCfg<(NPART == 2)>::S, BETA = OzCfg<(NPART == 2)>::BETA;
   const int k1 = k0 + K, rows = n - k1;
   const long gw = (blockIdx.x * (long)blockDim.x + threadIdx.x) / 32;
   const int lane = threadIdx.x % 32;
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const T* __restrict__ A, 
       y0 -= d0;   // exact: the remainder of an FP64 number after its nearest integer
       y1 -= d1;
       __nv_bfloat162 v;
-      v.x = __float2bfloat16_rn((float)d0);   // |d| <= 128: exact
+      v.x = __float2bfloat16_rn((float)d0);   // |d| <= 2^BETA: exact
       v.y = __float2bfloat16_rn((float)d1);
       *reinterpret_cast<__nv_bfloat162*>(pl + ((size_t)(p * S + s) * n + row) * K + 2 * lane) = v;
     }
@@ -338,7 +344,9 @@ bool make_map3(CUtensorMap* m, const void* base, int n, int planes, int box_rows
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t plane_bytes(int n, bool cplx) { return (size_t)(cplx ? 2 : 1) * S * n * ROWB; }
+size_t plane_bytes(int n, bool cplx) {
+  return cplx ? (size_t)2 * OzCfg<true>::S * n * ROWB : (size_t)OzCfg<false>::S * n * ROWB;
+}
 
 }  // namespace
 
@@ -351,7 +359,7 @@ cdwac_status ozaki_plan(cdwac_ctx* ctx, void* scratch, int n, bool cplx, OzakiPl
   plan->n = n;
   plan->cplx = cplx;
   Arena ar(scratch);
-  const int planes = (cplx ? 2 : 1) * S;
+  const int planes = cplx ? 2 * OzCfg<true>::S : OzCfg<false>::S;
   const int bn = cplx ? OzCfg<true>::BN : OzCfg<false>::BN;
   for (int b = 0; b < 2; ++b) {
     plan->wpl[b] = ar.take<char>(plane_bytes(n, cplx));
