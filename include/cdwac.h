@@ -195,8 +195,8 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
 typedef enum {
   CDWAC_LDLT_FP64 = 0,      /* every update on the FP64 FMA units */
   CDWAC_LDLT_EMULATED = 1   /* rank-64 trailing updates on the tcgen05 tensor cores from exact BF16 digits of
-                               the FP64 operands (8 digits of 7 bits per row, 36 digit products, exact FP32
-                               level sums recombined in FP64): FP64-equivalent accuracy */
+                               the FP64 operands (per row 7 digits of 8 bits, complex 8 of 7 bits; exact FP32
+                               level sums recombined in 64-bit integers): FP64-equivalent accuracy */
 } cdwac_ldlt_method;
 
 /* Square-root-free Cholesky factorisation A = L D L^T of the symmetric matrix I - Pi of Eq. bigLambda (real
