@@ -24,7 +24,11 @@
  *     a singular complex pivot, a wait that ran out) are OR-ed into a device status word; cdwac_sync_status
  *     waits for the stream and returns the first of them.  No call aborts, traps or waits without a bound.
  *   - A context serves one device and one stream at a time; calls that overlap on two streams race on its
- *     scratch.
+ *     scratch.  Internally a call may fork work from that stream onto the context's own streams (frequency
+ *     lanes, the factorisation's critical-path and side streams) and joins them back before it returns.
+ *   - Tuning read once when a context is created: CDWAC_FREQ_LANES (concurrent frequency lanes of a W build,
+ *     1..16, default 8, further limited to half of the free device memory), CDWAC_LOOKAHEAD (0 runs the
+ *     factorisation's bulk updates in line instead of on a side stream; default 1).
  */
 #ifndef CDWAC_H
 #define CDWAC_H
