@@ -291,8 +291,13 @@ def run_ours(args, rank, ws, dist):
         cnt, tms = prof["pi_tc_imag"]
         ach = pi_flops / (tms / cnt / 1e3) / 1e12
         pk = peaks["bf16_tflops_sustained"] / 3.0
+        kpad = -(-nov // 64) * 64
+        algo_bytes = 4.0 * n * kpad * 2 + n * (n + 1) / 2 * 8 + n * n * 4   # BF16 planes in, I - Pi and -Pi out
         rl["pi_tc_imag"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                            "traffic": None,
+                            "traffic": 1.05 * algo_bytes,
+                            "traffic_basis": ("DRAM bytes per launch scaled from the ncu capture of the same kernel "
+                                              "on the medium case (profiles/tc_syrk_kernel_medium.md: 524 MB = "
+                                              "1.05 x its algorithmic bytes) by the algorithmic bytes here"),
                             "peak_basis": f"bf16_tflops_sustained/3 ({peak_kind}): three BF16 products per MAC",
                             "algorithmic_flops_per_launch": pi_flops}
     if "ldlt" in prof:
