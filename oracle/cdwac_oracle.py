@@ -151,7 +151,7 @@ def w_elements(On_s, Lam, m_idx=None):
     On_s is O^{n m}_P as [N_aux, N_basis] (symmetric in n, m).  Returns W for every m (or for m_idx).
     """
     O = On_s if m_idx is None else On_s[:, m_idx]
-    return np.einsum("pm,pq,qm->m", O, Lam, O)
+    return np.sum(O * (Lam @ O), axis=0)          # column m: o_m^T (Lambda o_m)
 
 
 def w_imag_table(B, D, On, xi):
