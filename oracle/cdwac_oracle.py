@@ -107,6 +107,8 @@ def polarizability(B, D, z):
         w = 2.0 * (-2.0 * D / (z.imag ** 2 + D ** 2))
     else:
         w = 2.0 * (1.0 / (z - D) - 1.0 / (z + D))
+        # B is real: the real and imaginary parts of the sum are two real products
+        return (B * w.real[None, :]) @ B.T + 1j * ((B * w.imag[None, :]) @ B.T)
     return (B * w[None, :]) @ B.T
 
 
