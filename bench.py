@@ -25,6 +25,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The step runs ~25 streams (frequency lanes, each with critical-path and side streams); 32 hardware work queues
+# instead of the default 8 avoid false dependencies between them.  Read when CUDA initialises, so set before torch.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 METRIC = "core-state Sigma_c(w) evals/sec and QP solve time, CD-WAC vs plain CD on 1 GB300 at <=1 meV"
 UNIT = "Sigma_c evals/s"

@@ -28,7 +28,9 @@
  *     lanes, the factorisation's critical-path and side streams) and joins them back before it returns.
  *   - Tuning read once when a context is created: CDWAC_FREQ_LANES (concurrent frequency lanes of a W build,
  *     1..16, default 8, further limited to half of the free device memory), CDWAC_LOOKAHEAD (0 runs the
- *     factorisation's bulk updates in line instead of on a side stream; default 1).
+ *     factorisation's bulk updates in line instead of on a side stream; default 1).  A process that runs the
+ *     default eight lanes does best with CUDA_DEVICE_MAX_CONNECTIONS=32 set before CUDA initialises (bench.py
+ *     does so).
  */
 #ifndef CDWAC_H
 #define CDWAC_H
