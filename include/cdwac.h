@@ -60,9 +60,11 @@ typedef enum { CDWAC_F64 = 0, CDWAC_F32 = 1 } cdwac_dtype;
 /* Arithmetic of the W build.  FP64: every contraction in FP64 (parity path).  MIXED: Pi and the near-real
  * Pi(z) as split-BF16 (hi/lo, three products) tcgen05 tensor-core contractions with FP32 accumulation; the
  * Cholesky / LDL^T stays FP64-accurate (diagonal blocks and panels on the FP64 units, trailing updates as exact
- * BF16 digit products on the tensor cores, CDWAC_LDLT_EMULATED below); the W solves run in FP32 on the FP64
- * factor; the Thiele fit and the residue sum stay FP64; the I_n quadrature terms are FP32 with FP64 partial
- * sums. */
+ * BF16 digit products on the tensor cores, CDWAC_LDLT_EMULATED below); the W solves are blocked forward
+ * substitutions on the FP64 factor whose products run as split-BF16 tensor-core GEMMs (FP32 block solves, FP64
+ * sums of W); the Thiele fit and the residue sum stay FP64; the I_n quadrature terms are FP32 with FP64 partial
+ * sums.  The mixed form's W(z) error is the BF16x3 error of Pi (~2e-5 relative) times cond(I - Pi(z)): large for
+ * near-real points that lie among a strongly coupled system's excitations. */
 typedef enum { CDWAC_PREC_FP64 = 0, CDWAC_PREC_MIXED = 1 } cdwac_precision;
 
 typedef struct cdwac_ctx cdwac_ctx;
