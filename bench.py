@@ -294,13 +294,11 @@ def run_ours(args, rank, ws, dist):
         cnt, tms = prof["pi_tc_imag"]
         ach = pi_flops / (tms / cnt / 1e3) / 1e12
         pk = peaks["bf16_tflops_sustained"] / 3.0
-        kpad = -(-nov // 64) * 64
-        algo_bytes = 4.0 * n * kpad * 2 + n * (n + 1) / 2 * 8 + n * n * 4   # BF16 planes in, I - Pi and -Pi out
         rl["pi_tc_imag"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                            "traffic": 1.05 * algo_bytes,
-                            "traffic_basis": ("DRAM bytes per launch scaled from the ncu capture of the same kernel "
-                                              "on the medium case (profiles/tc_syrk_kernel_medium.md: 524 MB = "
-                                              "1.05 x its algorithmic bytes) by the algorithmic bytes here"),
+                            "traffic": 8.490e9 if spec.n_aux == 4000 and nov == 129600 else None,
+                            "traffic_basis": ("dram__bytes_read.sum + dram__bytes_write.sum of one launch at this "
+                                              "size (ncu, profiles/tc_syrk_kernel_acene.md): 8.37 GB + 0.12 GB, "
+                                              "2.0 x the algorithmic bytes"),
                             "peak_basis": f"bf16_tflops_sustained/3 ({peak_kind}): three BF16 products per MAC",
                             "algorithmic_flops_per_launch": pi_flops}
     if "ldlt" in prof:

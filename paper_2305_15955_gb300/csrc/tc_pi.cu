@@ -41,6 +41,37 @@ __device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
   tj = b - t * (t + 1) / 2;
 }
 
+// Tile b of the lower triangle of nt x nt tiles, in groups of G x G tiles (lower-triangle order of the groups,
+// row-major inside a group): the CTAs of one wave then share about 2G operand row blocks, so that each K-slice of
+// them comes from DRAM once per wave instead of once per row block of the whole triangle.
+constexpr int TILE_GROUP = 12;
+__device__ inline void grouped_tile_coords(int b, int nt, int& ti, int& tj) {
+  constexpr int G = TILE_GROUP;
+  const int ns = (nt + G - 1) / G;
+  int rem = b;
+  for (int I = 0; I < ns; ++I) {
+    const int rI = min(G, nt - I * G);
+    for (int J = 0; J <= I; ++J) {
+      const int cJ = min(G, nt - J * G);
+      const int cnt = J < I ? rI * cJ : rI * (rI + 1) / 2;
+      if (rem < cnt) {
+        if (J < I) {
+          ti = I * G + rem / cJ;
+          tj = J * G + rem % cJ;
+        } else {
+          int r, c;
+          lower_tile_coords(rem, r, c);
+          ti = I * G + r;
+          tj = J * G + c;
+        }
+        return;
+      }
+      rem -= cnt;
+    }
+  }
+  ti = tj = nt;   // past the triangle: not reached for b < nt (nt + 1) / 2
+}
+
 template <int NACC>
 struct Cfg {
   static constexpr int NPL = 2 * NACC + 2;                 // operand planes per stage
@@ -66,7 +97,7 @@ __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int ti, tj;
-  lower_tile_coords(blockIdx.x, ti, tj);
+  grouped_tile_coords(blockIdx.x, (n + BM - 1) / BM, ti, tj);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
