@@ -344,7 +344,7 @@ struct ImagBufs {
   double* V;
   void* tc_lane;
   float* negpi32;
-  void* ws32;
+  void* wsolve;
 };
 
 // FP64 path: W = y^T D^-1 u with u = L^-1 Pi o (needs Pi O and a second solve); mixed path: FP32 solves of the
@@ -369,7 +369,7 @@ static ImagBufs carve_imag(Arena& ar, const cdwac_system* sys, bool mixed) {
   b.V = mixed ? nullptr : ar.take<double>((size_t)sys->n_states * n * nb);
   b.tc_lane = mixed ? ar.take<char>(tc_pi_lane_bytes(n, n_ov, 1)) : nullptr;
   b.negpi32 = mixed ? ar.take<float>((size_t)n * n) : nullptr;
-  b.ws32 = mixed ? ar.take<char>(wsolve_tc_scratch_bytes(n, cols)) : nullptr;
+  b.wsolve = mixed ? ar.take<char>(wsolve_tc_scratch_bytes(n, cols)) : nullptr;
   b.oz = mixed ? ar.take<char>(ldlt_tc_scratch_bytes(n, false)) : nullptr;
   return b;
 }
@@ -396,7 +396,7 @@ static cdwac_status imag_freqs(cdwac_ctx* lc, const cdwac_system* sys, const cdw
     ProfScope ps(lc, PROF_QUADFORM, st);
     if (mixed) {
       rc = wsolve_tc(lc, b.f.A, b.f.dinv, b.f.linv, b.negpi32, n, sys->O_n, sys->O_dtype, (long)n * nb, nb,
-                    sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, b.ws32, st);
+                    sys->n_states, nb, W_imag + (long)k * nb, (long)prm->n_imag * nb, b.wsolve, st);
     } else {
       if ((rc = launch_pi_times_o(lc, b.f.A, b.pidiag, n, sys->O_n, sys->O_dtype, (long)n * nb, nb, sys->n_states, nb,
                                   b.V, st)))
