@@ -410,6 +410,15 @@ class QPResult:
     status: int            # 0 converged by fixed point, 1 by bracketed bisection, 2 not converged
 
 
+def spectral_function(sigma_c, eps_n, omega, shift=0.0):
+    """Diagonal spectral function A_nn(omega) = |Im[(omega - eps_n - shift - Sigma^c_n(omega))^{-1}]| / pi
+    (Sec. 5.4: the imaginary part of the Green's function, with shift = Sigma^x_n - v^xc_n as in Eq. qp_eq).
+    The paper gives A_nn up to a factor; 1/pi makes a single quasiparticle pole integrate to one.  sigma_c holds
+    Sigma^c_n at the points omega."""
+    g = 1.0 / (np.asarray(omega) - eps_n - shift - np.asarray(sigma_c))
+    return np.abs(g.imag) / np.pi
+
+
 def qp_solve(sigma_fn, eps_n, shift, omega_grid, tol=1e-7, max_iter=100, h=1e-5, bisect_tol=1e-9, upper=np.inf):
     """Solve e = eps_n + shift + Re Sigma^c_n(e) (Eq. qp_eq with shift = Sigma^x_n - v^xc_n).
 

@@ -278,3 +278,29 @@ def test_ldlt_reads_only_the_lower_triangle():
     L1, d1 = o.ldlt_nopivot(A)
     L2, d2 = o.ldlt_nopivot(Ag)
     assert np.array_equal(L1, L2) and np.array_equal(d1, d2)
+
+
+# ---- spectral function (Sec. 5.4) ---------------------------------------------------------------------------------
+
+def test_spectral_function_lorentzian_closed_form():
+    """A constant Sigma = -i gamma gives the Lorentzian gamma / pi / ((omega - eps - shift)^2 + gamma^2)."""
+    eps, shift, gamma = -10.6, 0.3, 0.05
+    w = np.linspace(-12.0, -8.0, 2001)
+    A = o.spectral_function(np.full(w.size, -1j * gamma), eps, w, shift)
+    ref = gamma / np.pi / ((w - eps - shift) ** 2 + gamma ** 2)
+    assert np.max(np.abs(A - ref)) < 1e-13 * ref.max()
+
+
+def test_spectral_function_sum_rule_one_pole_self_energy():
+    """Sigma(omega) = a / (omega - b + i eta): the quasiparticle and its satellite share unit spectral weight."""
+    eps, a, b, eta = -10.6, 0.4, -12.0, 2e-3
+    w = np.linspace(-40.0, 20.0, 1_200_001)
+    A = o.spectral_function(a / (w - b + 1j * eta), eps, w)
+    total = np.trapezoid(A, w)
+    assert abs(total - 1.0) < 2e-3, total
+    # both poles of G carry weight: solutions of (w - eps)(w - b) = a
+    disc = math.sqrt((eps - b) ** 2 + 4 * a)
+    w1, w2 = 0.5 * (eps + b + disc), 0.5 * (eps + b - disc)
+    z1 = (w1 - b) / (w1 - w2)
+    near1 = np.abs(w - w1) < 0.2
+    assert abs(np.trapezoid(A[near1], w[near1]) - z1) < 2e-2
