@@ -197,6 +197,18 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
+/* Diagonal spectral function (Sec. 5.4): A_nn(omega_j) = |Im[(omega_j - eps_n - shift_n - Sigma^c_n(omega_j))^-1]|
+ * / pi, the imaginary part of the Green's function (normalised so that one quasiparticle pole carries weight one).
+ * Sigma^c as in cdwac_sigma: CD-WAC from the continued fractions (pade != NULL) or plain CD (pade == NULL), which
+ * the paper compares for a 50 eV window at 0.01 eV spacing (5000 points).
+ *   shift    [n_states]                      in (may be NULL = 0): Sigma^x_n - v^xc_n.
+ *   omega    [n_omega]                       in: real frequencies (CD-WAC needs omega < eps_LUMO).
+ *   sigma    [n_states][n_omega][2]          out: Sigma^c_n(omega_j).
+ *   A        [n_states][n_omega]             out. */
+cdwac_status cdwac_spectral(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
+                            const double* omega, int n_omega, double* sigma, double* A, void* stream);
+
 /* ---- the factorisation step on its own -------------------------------------------------------------- */
 
 /* Trailing-update arithmetic of the LDL^T factorisation. */

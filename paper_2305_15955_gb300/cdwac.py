@@ -110,6 +110,7 @@ def load():
     lib.cdwac_launch_count.restype = ctypes.c_longlong
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
     lib.cdwac_ldlt_factor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+    lib.cdwac_spectral.argtypes = [P, sysp, prmp, P, P, P, padep, P, P, ctypes.c_int, P, P, P]
     lib.cdwac_mlp_features.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                        ctypes.c_int, P, P, P, P, P]
     lib.cdwac_mlp_loss_grad.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
@@ -319,6 +320,23 @@ class Context:
 
     def _dev(self):
         return torch.device("cuda", self.device)
+
+    def spectral(self, system: System, params: Params, xi, wxi, W_imag, pade: PadeModel | None, omega, shift=None,
+                 sync=True):
+        """cdwac_spectral: (Sigma^c [n_states, n_omega] complex, A [n_states, n_omega]) on the device."""
+        dev = self._dev()
+        omega = torch.as_tensor(omega, dtype=torch.float64).to(dev).contiguous()
+        sig = torch.empty(system.n_states, omega.numel(), dtype=torch.complex128, device=dev)
+        A = torch.empty(system.n_states, omega.numel(), dtype=torch.float64, device=dev)
+        sh = None if shift is None else torch.as_tensor(shift, dtype=torch.float64).to(dev).contiguous()
+        p = params.c()
+        pc = pade.c() if pade is not None else None
+        self._check(self.lib.cdwac_spectral(self.h, ctypes.byref(system.c), ctypes.byref(p), _ptr(xi), _ptr(wxi),
+                                            _ptr(W_imag), ctypes.byref(pc) if pc is not None else None, _ptr(sh),
+                                            _ptr(omega), int(omega.numel()), _ptr(sig), _ptr(A), self._stream()))
+        if sync:
+            self.sync_status()
+        return sig, A
 
     def ldlt_factor(self, A, method: int = LDLT_FP64, sync: bool = True):
         """cdwac_ldlt_factor in place on a square float64 or complex128 CUDA tensor (row-major, contiguous): the

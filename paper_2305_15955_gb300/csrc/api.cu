@@ -296,6 +296,17 @@ cdwac_status cdwac_ldlt_factor(cdwac_ctx* ctx, void* A, int n, int is_complex, i
   return ldlt_factor<double>(ctx, static_cast<double*>(A), n, dinv, linv, wpanel, st, oz);
 }
 
+cdwac_status cdwac_spectral(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
+                            const double* omega, int n_omega, double* sigma, double* A, void* stream) {
+  if (!ctx) return CDWAC_ERR_ARG;
+  if (!sigma || !A) return set_error(ctx, CDWAC_ERR_ARG, "null output");
+  cdwac_status rc = cdwac_sigma(ctx, sys, prm, xi, wxi, W_imag, pade, omega, n_omega, sigma, stream);
+  if (rc) return rc;
+  return launch_spectral(ctx, sys->eps, sys->states, sys->n_states, shift, omega, n_omega, sigma, A,
+                         (cudaStream_t)stream);
+}
+
 // ---- frequency lanes: the per-frequency work of one call split over concurrent streams -------------------------
 // Each lane owns a context (own scratch, own LDL^T side stream) and takes frequencies k = l, l + L, ...; the
 // caller's stream forks to the lanes and joins them.  While one lane walks the sequential diagonal/panel steps of

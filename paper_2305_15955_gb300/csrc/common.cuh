@@ -267,6 +267,8 @@ cdwac_status launch_near_real_points(cdwac_ctx* ctx, const double* eps, int n_oc
                                      int n_states, int n_real, double eta_ref, double margin, double* z_real,
                                      cudaStream_t st);
 // sigma.cu
+cdwac_status launch_spectral(cdwac_ctx* ctx, const double* eps, const int* states, int n_states, const double* shift,
+                             const double* omega, int n_omega, const double* sigma, double* A, cudaStream_t st);
 cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                               const double* wxi, const double* W_imag, const cdwac_pade* pade,
                               const double* omega, int n_omega, double* sigma, cudaStream_t st);

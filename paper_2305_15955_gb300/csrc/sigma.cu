@@ -265,7 +265,30 @@ SigmaArgs make_args(const cdwac_system* sys, const cdwac_params* prm, const doub
   return A;
 }
 
+// Diagonal spectral function (Sec. 5.4): A = |Im[(omega - eps_n - shift_n - Sigma^c_n(omega))^-1]| / pi
+//   = |Im d| / |d|^2 / pi,  d = omega - eps_n - shift_n - Sigma^c_n(omega).
+__global__ void spectral_kernel(const double* __restrict__ eps, const int* __restrict__ states, int n_states,
+                                const double* __restrict__ shift, const double* __restrict__ omega, int n_omega,
+                                const cplx* __restrict__ sigma, double* __restrict__ Aout) {
+  const long e = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (e >= (long)n_states * n_omega) return;
+  const int s = (int)(e / n_omega), j = (int)(e % n_omega);
+  const double dre = omega[j] - eps[states[s]] - (shift ? shift[s] : 0.0) - sigma[e].x;
+  const double dim = -sigma[e].y;
+  Aout[e] = fabs(dim) / (dre * dre + dim * dim) / 3.14159265358979323846;
+}
+
 }  // namespace
+
+cdwac_status launch_spectral(cdwac_ctx* ctx, const double* eps, const int* states, int n_states, const double* shift,
+                             const double* omega, int n_omega, const double* sigma, double* A, cudaStream_t st) {
+  const long total = (long)n_states * n_omega;
+  if (total <= 0) return CDWAC_OK;
+  spectral_kernel<<<(int)((total + 255) / 256), 256, 0, st>>>(eps, states, n_states, shift, omega, n_omega,
+                                                              reinterpret_cast<const cplx*>(sigma), A);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
 
 cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                               const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* omega,
