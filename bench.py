@@ -351,7 +351,7 @@ def run_ours(args, rank, ws, dist):
                                     "the CD-WAC iteration count + 2 (Z), extrapolated"}
         line["cdwac_vs_plain_cd_qp_speedup_extrapolated"] = line["plain_cd"]["qp_solve_s_extrapolated"] / (ms / 1e3)
 
-        # diagonal spectral function over the paper's window (Sec. 5.4): 50 eV at 0.01 eV, 5000 points from 15 eV
+        # diagonal spectral function over the paper's window (Sec. 5.5): 50 eV at 0.01 eV, 5000 points from 15 eV
         # below the core level (inside the near-real grid's reach), from the continued fractions; plain CD needs one
         # Pi(z) + LDL^T per residue at every point
         ev = 1.0 / 27.211386

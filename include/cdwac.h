@@ -197,7 +197,7 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
-/* Diagonal spectral function (Sec. 5.4): A_nn(omega_j) = |Im[(omega_j - eps_n - shift_n - Sigma^c_n(omega_j))^-1]|
+/* Diagonal spectral function (Sec. 5.5): A_nn(omega_j) = |Im[(omega_j - eps_n - shift_n - Sigma^c_n(omega_j))^-1]|
  * / pi, the imaginary part of the Green's function (normalised so that one quasiparticle pole carries weight one).
  * Sigma^c as in cdwac_sigma: CD-WAC from the continued fractions (pade != NULL) or plain CD (pade == NULL), which
  * the paper compares for a 50 eV window at 0.01 eV spacing (5000 points).

@@ -350,6 +350,45 @@ def near_real_points(eps, n_occ, eps_states, n_real, eta_ref=1e-3, margin=0.5):
     return x + 1j * eta_ref
 
 
+def _neighbourhood(c_lo, c_hi, delta, n):
+    """n equidistant abscissae on the neighbourhood of radius delta around the centres [c_lo, c_hi], cut to the
+    first quadrant (Re z >= 0, Sec. 3.3): [max(0, c_lo - delta), c_hi + delta], both ends included; a single point
+    sits at the middle of the centres."""
+    if n == 0:
+        return np.zeros(0)
+    if n == 1:
+        return np.array([max(0.0, 0.5 * (c_lo + c_hi))])
+    return np.linspace(max(0.0, c_lo - delta), c_hi + delta, n)
+
+
+def refined_reference_points(eps, n_occ, eps_states, n_core, n_val, delta_c, delta_v, eta_ref=1e-3):
+    """Refined near-real reference set omega_C U omega_V (Sec. 3.3), n_core + n_val points x_j + i eta_ref.
+
+    omega_C: a neighbourhood of radius delta_c around the typical core-level residue |eps_c - omega|, taken at
+    omega = eps_n with eps_c a requested core level, i.e. the centres |eps_n' - eps_n| over the requested states
+    (0 for one state).  omega_V: a neighbourhood of radius delta_v around the valence residue |eps_F - omega| at
+    omega = eps_n, i.e. the centres |eps_F - eps_n|.  One set per system, like the generic set; points lie in the
+    first quadrant.  The Pade order of the paper's CD-WAC(N_core, N_valence, N_Im) is the sum of the three sizes."""
+    e = np.atleast_1d(np.asarray(eps_states, dtype=float))
+    ef = fermi_level(eps, n_occ)
+    xc = _neighbourhood(0.0, float(e.max() - e.min()), delta_c, n_core)
+    rv = np.abs(ef - e)
+    xv = _neighbourhood(float(rv.min()), float(rv.max()), delta_v, n_val)
+    return np.concatenate([xc, xv]) + 1j * eta_ref
+
+
+def reference_points(eps, n_occ, eps_states, params):
+    """F_real of Sec. 3.3 for params.real_set: "generic" (omega_G) or "refined" (omega_C U omega_V)."""
+    if params.real_set == "generic":
+        return near_real_points(eps, n_occ, eps_states, params.n_real, params.eta_ref, params.real_margin)
+    if params.real_set == "refined":
+        if params.n_core + params.n_val != params.n_real:
+            raise ValueError("the refined set needs n_real = n_core + n_val")
+        return refined_reference_points(eps, n_occ, eps_states, params.n_core, params.n_val, params.delta_c,
+                                        params.delta_v, params.eta_ref)
+    raise ValueError(f"unknown reference set {params.real_set!r}")
+
+
 @dataclasses.dataclass
 class WacModel:
     """CD-WAC continuation of one state: one Thiele fit per occupied m."""
@@ -412,7 +451,7 @@ class QPResult:
 
 def spectral_function(sigma_c, eps_n, omega, shift=0.0):
     """Diagonal spectral function A_nn(omega) = |Im[(omega - eps_n - shift - Sigma^c_n(omega))^{-1}]| / pi
-    (Sec. 5.4: the imaginary part of the Green's function, with shift = Sigma^x_n - v^xc_n as in Eq. qp_eq).
+    (Sec. 5.5: the imaginary part of the Green's function, with shift = Sigma^x_n - v^xc_n as in Eq. qp_eq).
     The paper gives A_nn up to a factor; 1/pi makes a single quasiparticle pole integrate to one.  sigma_c holds
     Sigma^c_n at the points omega."""
     g = 1.0 / (np.asarray(omega) - eps_n - shift - np.asarray(sigma_c))
@@ -513,6 +552,11 @@ class Params:
     greedy_criterion: str = "max"
     real_margin: float = 0.5
     pade_tol: float = 0.0
+    real_set: str = "generic"      # "generic" (omega_G) or "refined" (omega_C U omega_V), Sec. 3.3
+    n_core: int = 20               # refined set sizes; CD-WAC(20, 20, N_Im) is the paper's recommendation (Sec. 5.1)
+    n_val: int = 20
+    delta_c: float = 0.5           # neighbourhood radii (Ha), "parameters that can be tuned" (Sec. 3.3)
+    delta_v: float = 1.0
 
 
 def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None, with_sigma=True):
@@ -520,7 +564,7 @@ def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=N
     occupied m, Sigma^c on omega_grid and the QP solution per state."""
     xi, wxi = imaginary_grid(params.n_imag, params.omega0)
     Wim = w_imag_table(B, D, On, xi)
-    zr = near_real_points(eps, n_occ, eps[list(states)], params.n_real, params.eta_ref, params.real_margin)
+    zr = reference_points(eps, n_occ, eps[list(states)], params)
     Wre_all = w_complex_table(B, D, On, zr, np.arange(n_occ)) if len(zr) else None
     out = {"xi": xi, "wxi": wxi, "W_imag": Wim, "z_real": zr, "states": []}
     for s, n in enumerate(states):

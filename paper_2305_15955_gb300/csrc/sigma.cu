@@ -265,7 +265,7 @@ SigmaArgs make_args(const cdwac_system* sys, const cdwac_params* prm, const doub
   return A;
 }
 
-// Diagonal spectral function (Sec. 5.4): A = |Im[(omega - eps_n - shift_n - Sigma^c_n(omega))^-1]| / pi
+// Diagonal spectral function (Sec. 5.5): A = |Im[(omega - eps_n - shift_n - Sigma^c_n(omega))^-1]| / pi
 //   = |Im d| / |d|^2 / pi,  d = omega - eps_n - shift_n - Sigma^c_n(omega).
 __global__ void spectral_kernel(const double* __restrict__ eps, const int* __restrict__ states, int n_states,
                                 const double* __restrict__ shift, const double* __restrict__ omega, int n_omega,

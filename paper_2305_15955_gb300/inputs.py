@@ -2,7 +2,7 @@
 
 This module holds none of the method's arithmetic.  It only draws the mean-field input of a G0W0 run
 (the eigenvalues eps_m and the RI-V tensors O^{nm}_P of Eq. 3c_OnmP in Sec. 2.2) for synthetic systems whose
-shapes follow the paper's acene and amorphous-carbon workloads (Sec. 5.4).  Both the CUDA path and the CPU
+shapes follow the paper's acene and amorphous-carbon workloads (Sec. 5.5).  Both the CUDA path and the CPU
 oracle consume the buffers built here.
 
 Random numbers are counter based, so any block of the symmetric tensor O^{pq}_P can be drawn without

@@ -1,4 +1,4 @@
-"""Diagonal spectral function (Sec. 5.4) through cdwac_spectral against the oracle.
+"""Diagonal spectral function (Sec. 5.5) through cdwac_spectral against the oracle.
 
 A_nn(omega) = |Im[(omega - eps_n - shift_n - Sigma^c_n(omega))^-1]| / pi on the paper's window: 50 eV at 0.01 eV
 spacing (5000 points) from 15 eV below to 35 eV above the core level of the small system.  The CD-WAC self-energy is compared with the

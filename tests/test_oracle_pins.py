@@ -224,6 +224,62 @@ def test_cdwac_core_qp_close_to_cd(small):
     assert abs(e_cd - e_wac) * 27211.386 < 0.01          # well inside 1 meV with 40 near-real points
 
 
+def test_refined_reference_set_hand_example():
+    # eps_F = (eps_HOMO + eps_LUMO)/2 = 0; states 0 and 1 at -10.0 and -9.9 (Sec. 3.3, first quadrant only):
+    # core centres |eps_n' - eps_n| span [0, 0.1], radius 0.2 -> [0, 0.3]; 4 points 0, 0.1, 0.2, 0.3
+    # valence centres |eps_F - eps_n| span [9.9, 10.0], radius 0.5 -> [9.4, 10.5]; 3 points 9.4, 9.95, 10.5
+    eps = np.array([-10.0, -9.9, -1.0, -0.5, 0.5, 2.0])
+    z = o.refined_reference_points(eps, 4, eps[[0, 1]], 4, 3, 0.2, 0.5, eta_ref=2e-3)
+    np.testing.assert_allclose(z.real, [0.0, 0.1, 0.2, 0.3, 9.4, 9.95, 10.5], rtol=0, atol=1e-14)
+    assert np.all(z.imag == 2e-3)
+    # one state: the core centre is 0, so the neighbourhood is [0, delta_c]; a single valence point sits on
+    # the centre 10.0; an empty region contributes nothing
+    z = o.refined_reference_points(eps, 4, eps[[0]], 3, 1, 0.2, 0.5)
+    np.testing.assert_allclose(z.real, [0.0, 0.1, 0.2, 10.0], rtol=0, atol=1e-14)
+    assert len(o.refined_reference_points(eps, 4, eps[[0]], 0, 2, 0.2, 0.5)) == 2
+    # a valence radius wider than the centre is cut at Re z = 0
+    z = o.refined_reference_points(eps, 4, eps[[0]], 0, 2, 0.2, 12.0)
+    np.testing.assert_allclose(z.real, [0.0, 22.0], rtol=0, atol=1e-13)
+
+
+def test_refined_set_cdwac_exact_for_few_poles():
+    # n_basis 4, n_occ 2: four transitions, so W_nm(z) is a sum of four poles in z^2, a rational function of
+    # type [3/4] in z^2; eight Thiele nodes reproduce it exactly and CD-WAC then equals plain CD.  With two
+    # imaginary nodes the fit has to take at least six of the refined points.
+    rng = np.random.default_rng(11)
+    eps = np.array([-10.0, -0.6, 0.3, 1.1])
+    B = rng.normal(size=(6, 4)) / np.sqrt(6)
+    On = rng.normal(size=(1, 6, 4)) / np.sqrt(6)
+    D = o.transition_energies(eps, 2)
+    P = o.Params(n_imag=2, n_real=8, pade_M=8, eta=1e-3, real_set="refined", n_core=4, n_val=4, delta_c=0.4,
+                 delta_v=0.8)
+    grid = np.linspace(-10.5, -10.05, 7)
+    wac = o.run_cdwac(B, D, On, eps, 2, [0], P, grid)
+    cd = o.run_cd(B, D, On, eps, 2, [0], P, grid)
+    assert sum(k >= 2 for k in wac["states"][0]["model"].fits[0].nodes) >= 6
+    s_w, s_c = wac["states"][0]["sigma"], cd["states"][0]["sigma"]
+    assert np.max(np.abs(s_w - s_c)) < 1e-9 * np.max(np.abs(s_c))
+
+
+def test_refined_set_brings_core_qp_to_cd(small):
+    # measured, not pinned: CD-WAC(20, 20, 100) against plain CD on the small system; without near-real points
+    # the same fit is several meV off (Sec. 5.1 reports the refined set reaching meV-level MAEs)
+    s = small
+    grid = inputs.omega_grid(128)
+    cd = o.run_cd(s["B"], s["D"], s["On"], s["eps"], 5, [0], o.Params(n_imag=100, n_real=0), grid,
+                  with_sigma=False)
+    e_cd = cd["states"][0]["qp"].e_qp
+    P = o.Params(n_imag=100, n_real=40, pade_M=64, real_set="refined", n_core=20, n_val=20)
+    wac = o.run_cdwac(s["B"], s["D"], s["On"], s["eps"], 5, [0], P, grid, with_sigma=False)
+    im = o.run_cdwac(s["B"], s["D"], s["On"], s["eps"], 5, [0], o.Params(n_imag=100, n_real=0, pade_M=64), grid,
+                     with_sigma=False)
+    err = abs(wac["states"][0]["qp"].e_qp - e_cd) * 27211.386
+    err_im = abs(im["states"][0]["qp"].e_qp - e_cd) * 27211.386
+    assert err < 0.1 and err_im > 1.0, (err, err_im)
+    with pytest.raises(ValueError):
+        o.reference_points(s["eps"], 5, s["eps"][[0]], o.Params(n_real=39, real_set="refined"))
+
+
 def test_thiele_replay_of_greedy_order_is_identical(small):
     s = small
     zr = o.near_real_points(s["eps"], 5, s["eps"][[0]], 20)
@@ -280,7 +336,7 @@ def test_ldlt_reads_only_the_lower_triangle():
     assert np.array_equal(L1, L2) and np.array_equal(d1, d2)
 
 
-# ---- spectral function (Sec. 5.4) ---------------------------------------------------------------------------------
+# ---- spectral function (Sec. 5.5) ---------------------------------------------------------------------------------
 
 def test_spectral_function_lorentzian_closed_form():
     """A constant Sigma = -i gamma gives the Lorentzian gamma / pi / ((omega - eps - shift)^2 + gamma^2)."""
