@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain-CD and CPU-baseline measurements")
     ap.add_argument("--n-imag", type=int, default=100, help="imaginary grid points (100 = the workload's value)")
     ap.add_argument("--n-real", type=int, default=40, help="near-real reference points (40 = the workload's value)")
+    ap.add_argument("--refined-map", action="store_true",
+                    help="instead of the step: QP error of CD-WAC(N_core, N_val, N_Im) against plain CD over a grid "
+                         "of refined-set sizes (one JSON line)")
     return ap.parse_args()
 
 
@@ -500,11 +503,77 @@ def run_batch(args, rank, ws, dist):
     ctx.close()
 
 
+def run_refined_map(args, rank, ws, dist):
+    """QP error of CD-WAC(N_core, N_val, N_Im) against plain CD, both FP64 on the same GPU: the synthetic analogue
+    of the reference-set calibration of Sec. 5.1.  A reduced acene-like system (N_basis 200 with 6 core levels at
+    -10.6 +- 0.01 Ha, 14 valence levels, 180 log-spaced virtuals; N_aux 600; seed 1) and its six core states;
+    100 imaginary points; Pade order M = N_core + N_val + N_Im as in the paper.  Also the generic set at the same
+    point counts and the time of each fit (near-real W build + greedy Thiele)."""
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2305_15955_gb300 import cdwac, inputs
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    g.build()
+    spec = inputs.custom_system(200, 20, 600, seed=1, n_core=6, states=tuple(range(6)))
+    eps = inputs.eigenvalues(spec)
+    sysd = cdwac.System(eps, inputs.build_B(spec), inputs.build_On(spec), spec.states, spec.n_occ)
+    ctx = cdwac.Context(0)
+    omega = inputs.omega_grid(128)
+    ni = args.n_imag
+    base = cdwac.Params(n_imag=ni, n_real=0, pade_M=min(cdwac.MAX_M, ni))
+    xi, wxi, W = ctx.build_W_imag(sysd, base)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_cd, _, _, qs_cd = ctx.qp_solve(sysd, base, xi, wxi, W, None, omega)
+    t_cd = time.perf_counter() - t0
+    e_cd = e_cd.cpu().numpy()
+
+    def measure(p):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        pade = ctx.fit_pade(sysd, p, xi, W)
+        torch.cuda.synchronize()
+        t_fit = time.perf_counter() - t
+        e, _, _, qs = ctx.qp_solve(sysd, p, xi, wxi, W, pade, omega)
+        err = np.abs(e.cpu().numpy() - e_cd) / HA_PER_MEV
+        return float(err.mean()), float(err.max()), 1e3 * t_fit, int(qs.cpu().numpy().max())
+
+    sizes = (0, 5, 10, 20, 40)
+    mae, mx, ms, st = ([[None] * len(sizes) for _ in sizes] for _ in range(4))
+    for i, nc in enumerate(sizes):
+        for j, nv in enumerate(sizes):
+            p = (cdwac.Params.refined(nc, nv, n_imag=ni, pade_M=min(cdwac.MAX_M, ni + nc + nv)) if nc + nv
+                 else base)
+            mae[i][j], mx[i][j], ms[i][j], st[i][j] = measure(p)
+    generic = {}
+    for nr in (10, 20, 40, 80):
+        generic[nr] = measure(cdwac.Params(n_imag=ni, n_real=nr, pade_M=min(cdwac.MAX_M, ni + nr)))
+    line = {"metric": "core QP error of CD-WAC(N_core, N_val, N_Im) against plain CD", "unit": "meV",
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "reduced acene-like: N_basis=200 (6 core at -10.6+-0.01 Ha, 14 valence in "
+                                   "[-1.2,-0.25], 180 virtual log-spaced in [0.01,5]), N_aux=600, seed 1, core "
+                                   "states 0-5; 128 omega in [-11,-10] Ha", "n_imag": ni,
+                       "delta_c_Ha": 0.5, "delta_v_Ha": 1.0, "pade_M": "N_core + N_val + N_Im"},
+            "sizes": list(sizes), "rows": "N_core", "cols": "N_val",
+            "mae_meV": mae, "max_meV": mx, "fit_ms": ms, "max_qp_status": st,
+            "generic": {str(k): {"mae_meV": v[0], "max_meV": v[1], "fit_ms": v[2], "max_qp_status": v[3]}
+                        for k, v in generic.items()},
+            "plain_cd_qp_s": t_cd, "plain_cd_qp_status": qs_cd.cpu().numpy().tolist()}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     rank, ws, dist = dist_init()
     if args.impl == "reference":
         run_reference(args, rank, ws, dist)
+    elif args.refined_map:
+        run_refined_map(args, rank, ws, dist)
     elif args.workload == "batch":
         run_batch(args, rank, ws, dist)
     else:

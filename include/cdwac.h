@@ -67,6 +67,17 @@ typedef enum { CDWAC_F64 = 0, CDWAC_F32 = 1 } cdwac_dtype;
  * near-real points that lie among a strongly coupled system's excitations. */
 typedef enum { CDWAC_PREC_FP64 = 0, CDWAC_PREC_MIXED = 1 } cdwac_precision;
 
+/* Near-real reference set F_real of the core-state CD-WAC (Sec. 3.3); every point is x_j + i eta_ref with x_j >= 0
+ * (first quadrant), one set per system shared by its requested states.
+ *   GENERIC  omega_G: n_real equidistant x_j on [0, max_n |eps_F - eps_n| + real_margin], both ends included.
+ *   REFINED  omega_C U omega_V, n_real = n_core + n_val: n_core equidistant x_j on the core neighbourhood
+ *            [0, max_n eps_n - min_n eps_n + delta_c] (radius delta_c around the core-level residues |eps_n' - eps_n|
+ *            at omega = eps_n, 0 for one state), then n_val equidistant x_j on the valence neighbourhood
+ *            [max(0, min_n r_n - delta_v), max_n r_n + delta_v], r_n = |eps_F - eps_n|.  A region of one point
+ *            holds the middle of its centres; an empty region holds none.
+ * eps_F = (eps_HOMO + eps_LUMO) / 2 and n runs over the requested states. */
+typedef enum { CDWAC_REAL_GENERIC = 0, CDWAC_REAL_REFINED = 1 } cdwac_real_set;
+
 typedef struct cdwac_ctx cdwac_ctx;
 
 /* One closed-shell system in the RI-V representation (Sec. 2.2).
@@ -89,9 +100,9 @@ typedef struct {
 typedef struct {
   int n_imag;          /* imaginary-axis Gauss-Legendre points (100) */
   double omega0;       /* grid map xi = omega0 (1 + x) / (1 - x) (1.0 Ha) */
-  int n_real;          /* near-real reference points per state, generic set omega_G (40; 0 = imaginary only) */
+  int n_real;          /* near-real reference points per state (40; 0 = imaginary only), set chosen by real_set */
   double eta_ref;      /* imaginary part of the near-real points (1e-3 Ha) */
-  double real_margin;  /* near-real points span [0, |eps_F - eps_n| + real_margin] (0.5 Ha) */
+  double real_margin;  /* GENERIC points span [0, |eps_F - eps_n| + real_margin] (0.5 Ha) */
   double eta;          /* broadening i*eta in I_n and R_n (1e-3 Ha) */
   int pade_M;          /* continued-fraction nodes per fit (64), at most n_imag + n_real and CDWAC_MAX_M */
   int greedy_first;    /* first node: 0 = argmax |W|, 1 = argmax Re W, 2 = candidate 0 */
@@ -99,6 +110,11 @@ typedef struct {
   int precision;       /* cdwac_precision */
   double pade_tol;     /* optional early end of a fit: stop once every remaining candidate is reproduced to an
                           L1 error below pade_tol * max|W| (0 = off, the paper's fixed M; default 0) */
+  int real_set;        /* cdwac_real_set (GENERIC) */
+  int n_core, n_val;   /* REFINED region sizes, n_core + n_val must equal n_real (20, 20: the paper's
+                          CD-WAC(20, 20, N_Im) of Sec. 5.1); ignored by GENERIC */
+  double delta_c;      /* REFINED core and valence neighbourhood radii (0.5 Ha, 1.0 Ha; Sec. 3.3 leaves them to */
+  double delta_v;      /*   tuning) */
 } cdwac_params;
 
 #define CDWAC_MAX_M 256          /* largest continued fraction the fit kernel holds */
@@ -162,8 +178,8 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
 
 /* Near-real reference points, W there, and the greedy Thiele fits: the wmatrix(F_real) and AC steps.
  *   xi, W_imag                               in: output of cdwac_build_W_imag with the same prm.
- *   z_real   [n_states][n_real][2]           out (may be NULL): x_j + i eta_ref, x_j equidistant in
- *                                            [0, |eps_F - eps_n| + real_margin], eps_F = (HOMO + LUMO) / 2.
+ *   z_real   [n_states][n_real][2]           out (may be NULL): x_j + i eta_ref, the generic or refined set
+ *                                            of prm->real_set (cdwac_real_set above).
  *   W_real   [n_states][n_real][n_occ][2]    out (may be NULL): W_nm(z_j) for the occupied m.
  *   pade                                     out: one fit per (n, occupied m) over the n_imag + n_real
  *                                            candidates (greedy ordering of Sec. 3.2).

@@ -24,6 +24,7 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_CUDA", "ERR_NOT_SPD", "ERR_SINGULAR", "ERR
 F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 LDLT_FP64, LDLT_EMULATED = 0, 1
+REAL_GENERIC, REAL_REFINED = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
@@ -52,7 +53,9 @@ class _Params(ctypes.Structure):
     _fields_ = [("n_imag", ctypes.c_int), ("omega0", ctypes.c_double), ("n_real", ctypes.c_int),
                 ("eta_ref", ctypes.c_double), ("real_margin", ctypes.c_double), ("eta", ctypes.c_double),
                 ("pade_M", ctypes.c_int), ("greedy_first", ctypes.c_int), ("greedy_crit", ctypes.c_int),
-                ("precision", ctypes.c_int), ("pade_tol", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("pade_tol", ctypes.c_double), ("real_set", ctypes.c_int),
+                ("n_core", ctypes.c_int), ("n_val", ctypes.c_int), ("delta_c", ctypes.c_double),
+                ("delta_v", ctypes.c_double)]
 
 
 class _ProfEntry(ctypes.Structure):
@@ -140,10 +143,22 @@ class Params:
     greedy_crit: int = 0
     precision: int = PREC_FP64
     pade_tol: float = 0.0
+    real_set: int = REAL_GENERIC
+    n_core: int = 20
+    n_val: int = 20
+    delta_c: float = 0.5
+    delta_v: float = 1.0
+
+    @classmethod
+    def refined(cls, n_core=20, n_val=20, delta_c=0.5, delta_v=1.0, **kw):
+        """CD-WAC(n_core, n_val, n_imag): the refined near-real set omega_C U omega_V (Sec. 3.3)."""
+        return cls(n_real=n_core + n_val, real_set=REAL_REFINED, n_core=n_core, n_val=n_val, delta_c=delta_c,
+                   delta_v=delta_v, **kw)
 
     def c(self) -> _Params:
         return _Params(self.n_imag, self.omega0, self.n_real, self.eta_ref, self.real_margin, self.eta, self.pade_M,
-                       self.greedy_first, self.greedy_crit, self.precision, self.pade_tol)
+                       self.greedy_first, self.greedy_crit, self.precision, self.pade_tol, self.real_set,
+                       self.n_core, self.n_val, self.delta_c, self.delta_v)
 
 
 def _ptr(t):

@@ -189,6 +189,11 @@ void cdwac_default_params(cdwac_params* p) {
   p->greedy_crit = 0;
   p->precision = CDWAC_PREC_FP64;
   p->pade_tol = 0.0;
+  p->real_set = CDWAC_REAL_GENERIC;
+  p->n_core = 20;
+  p->n_val = 20;
+  p->delta_c = 0.5;
+  p->delta_v = 1.0;
 }
 
 cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream) {
@@ -230,6 +235,13 @@ static cdwac_status check_system(cdwac_ctx* ctx, const cdwac_system* s, const cd
     return set_error(ctx, CDWAC_ERR_ARG, "omega0, eta_ref must be > 0 and eta >= 0");
   if (p->precision != CDWAC_PREC_FP64 && p->precision != CDWAC_PREC_MIXED)
     return set_error(ctx, CDWAC_ERR_ARG, "bad precision");
+  if (p->real_set != CDWAC_REAL_GENERIC && p->real_set != CDWAC_REAL_REFINED)
+    return set_error(ctx, CDWAC_ERR_ARG, "bad real_set");
+  if (p->real_set == CDWAC_REAL_REFINED &&
+      (p->n_core < 0 || p->n_val < 0 || p->n_core + p->n_val != p->n_real || !(p->delta_c >= 0) ||
+       !(p->delta_v >= 0) || !(p->delta_c < 1e6) || !(p->delta_v < 1e6)))
+    return set_error(ctx, CDWAC_ERR_ARG, "refined set: need n_core, n_val >= 0 with n_core + n_val = n_real and "
+                                         "finite delta_c, delta_v >= 0");
   if ((long)s->n_aux * s->n_aux > (1L << 31) * 16) return set_error(ctx, CDWAC_ERR_ARG, "n_aux too large");
   return CDWAC_OK;
 }
@@ -560,8 +572,8 @@ cdwac_status cdwac_fit_pade(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
   if (nr > 0) {
     void* tc_shared = mixed ? ar.take<char>(tc_pi_shared_bytes(n, n_ov)) : nullptr;
     if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
-    if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, nr, prm->eta_ref, prm->real_margin,
-                                      reinterpret_cast<double*>(zr), st)))
+    if ((rc = launch_near_real_points(ctx, sys->eps, n_occ, sys->states, ns, prm, reinterpret_cast<double*>(zr),
+                                      st)))
       return rc;
     if (mixed) {
       ProfScope ps(ctx, PROF_PI_PREP, st);

@@ -264,8 +264,7 @@ cdwac_status launch_thiele_fit(cdwac_ctx* ctx, int n_states, int n_occ, int n_im
                                const double* W_imag, int n_basis, const double* z_real, const double* W_real,
                                const cdwac_params* prm, const cdwac_pade* pade, cudaStream_t st);
 cdwac_status launch_near_real_points(cdwac_ctx* ctx, const double* eps, int n_occ, const int* states,
-                                     int n_states, int n_real, double eta_ref, double margin, double* z_real,
-                                     cudaStream_t st);
+                                     int n_states, const cdwac_params* prm, double* z_real, cudaStream_t st);
 // sigma.cu
 cdwac_status launch_spectral(cdwac_ctx* ctx, const double* eps, const int* states, int n_states, const double* shift,
                              const double* omega, int n_omega, const double* sigma, double* A, cudaStream_t st);

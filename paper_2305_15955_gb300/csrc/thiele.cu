@@ -157,24 +157,44 @@ __global__ void thiele_fit_kernel(int n_states, int n_occ, int n_imag, int n_rea
   }
 }
 
-// z_j = x_j + i eta_ref, x_j = j * top / (n_real - 1), x_{n_real-1} = top, top = max_n |eps_F - eps_n| + margin
+// n equidistant abscissae on the neighbourhood of radius delta around the centres [c_lo, c_hi], cut to Re z >= 0:
+// [max(0, c_lo - delta), c_hi + delta] with both ends; x_j = j * step + lo (product and sum rounded separately),
+// the last one exactly hi; a single point at the middle of the centres.
+__device__ double region_point(double c_lo, double c_hi, double delta, int n, int j) {
+  if (n == 1) return fmax(0.0, 0.5 * (c_lo + c_hi));
+  const double lo = fmax(0.0, c_lo - delta), hi = c_hi + delta;
+  if (j == n - 1) return hi;
+  return __dadd_rn(__dmul_rn((double)j, (hi - lo) / (double)(n - 1)), lo);
+}
+
+// Near-real reference points z_j = x_j + i eta_ref (Sec. 3.3), one set per system spanning the residues of every
+// requested state n, so that each Pi(z_j) + LDL^T serves all of them.
+//   generic  omega_G: x_j = j * top / (n_real - 1), x_{n_real-1} = top, top = max_n |eps_F - eps_n| + margin
+//   refined  omega_C: n_core points around the core-level residues |eps_n' - eps_n| at omega = eps_n (radius
+//            delta_c), then omega_V: n_real - n_core points around r_n = |eps_F - eps_n| (radius delta_v)
 __global__ void near_real_kernel(const double* eps, int n_occ, const int* states, int n_states, int n_real,
-                                 double eta_ref, double margin, cplx* z_real) {
+                                 int refined, int n_core, double delta_c, double delta_v, double eta_ref,
+                                 double margin, cplx* z_real) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= n_states * n_real) return;
-  int s = idx / n_real, j = idx % n_real;
-  // one grid per system: it spans the residues of every requested state
-  double ef = 0.5 * (eps[n_occ - 1] + eps[n_occ]);
-  double top = 0.0;
-  for (int t = 0; t < n_states; ++t) top = fmax(top, fabs(ef - eps[states[t]]));
-  top += margin;
-  (void)s;
+  const int j = idx % n_real;
+  const double ef = 0.5 * (eps[n_occ - 1] + eps[n_occ]);
+  double e_lo = eps[states[0]], e_hi = e_lo, r_lo = fabs(ef - e_lo), r_hi = r_lo;
+  for (int t = 1; t < n_states; ++t) {
+    const double e = eps[states[t]], r = fabs(ef - e);
+    e_lo = fmin(e_lo, e);
+    e_hi = fmax(e_hi, e);
+    r_lo = fmin(r_lo, r);
+    r_hi = fmax(r_hi, r);
+  }
   double x;
-  if (n_real == 1) {
-    x = 0.0;
+  if (!refined) {
+    const double top = r_hi + margin;
+    x = n_real == 1 ? 0.0 : (j == n_real - 1 ? top : (double)j * (top / (double)(n_real - 1)));
+  } else if (j < n_core) {
+    x = region_point(0.0, e_hi - e_lo, delta_c, n_core, j);
   } else {
-    double step = top / (double)(n_real - 1);
-    x = (j == n_real - 1) ? top : (double)j * step;
+    x = region_point(r_lo, r_hi, delta_v, n_real - n_core, j - n_core);
   }
   z_real[idx] = mkc(x, eta_ref);
 }
@@ -182,11 +202,13 @@ __global__ void near_real_kernel(const double* eps, int n_occ, const int* states
 }  // namespace
 
 cdwac_status launch_near_real_points(cdwac_ctx* ctx, const double* eps, int n_occ, const int* states, int n_states,
-                                     int n_real, double eta_ref, double margin, double* z_real, cudaStream_t st) {
-  int n = n_states * n_real;
+                                     const cdwac_params* prm, double* z_real, cudaStream_t st) {
+  const int n = n_states * prm->n_real;
   if (n == 0) return CDWAC_OK;
-  near_real_kernel<<<ceil_div(n, 128), 128, 0, st>>>(eps, n_occ, states, n_states, n_real, eta_ref, margin,
-                                                      reinterpret_cast<cplx*>(z_real));
+  const bool refined = prm->real_set == CDWAC_REAL_REFINED;
+  near_real_kernel<<<ceil_div(n, 128), 128, 0, st>>>(eps, n_occ, states, n_states, prm->n_real, refined ? 1 : 0,
+                                                      refined ? prm->n_core : 0, prm->delta_c, prm->delta_v,
+                                                      prm->eta_ref, prm->real_margin, reinterpret_cast<cplx*>(z_real));
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }

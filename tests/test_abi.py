@@ -31,6 +31,10 @@ def test_default_params_and_errors_without_gpu():
     lib.cdwac_default_params(ctypes.byref(p))
     d = cdwac.Params()
     assert (p.n_imag, p.n_real, p.pade_M, p.eta, p.eta_ref) == (d.n_imag, d.n_real, d.pade_M, d.eta, d.eta_ref)
+    assert (p.real_set, p.n_core, p.n_val, p.delta_c, p.delta_v) == (d.real_set, d.n_core, d.n_val, d.delta_c,
+                                                                      d.delta_v)
+    # the library filled the binding's struct up to its last field (zero-initialised before the call)
+    assert p.delta_v == 1.0
     # null arguments are rejected on the host, before any CUDA call
     assert lib.cdwac_create(None, 0) == cdwac.ERR_ARG
     assert lib.cdwac_build_W_imag(None, None, None, None, None, None, None) == cdwac.ERR_ARG

@@ -39,7 +39,9 @@ def make(spec, dtype=np.float64, states=None):
 def oracle_params(p: cdwac.Params):
     return o.Params(n_imag=p.n_imag, omega0=p.omega0, n_real=p.n_real, eta_ref=p.eta_ref, eta=p.eta,
                     pade_M=p.pade_M, greedy_first=["absmax", "max", "first"][p.greedy_first],
-                    greedy_criterion=["max", "min"][p.greedy_crit], real_margin=p.real_margin, pade_tol=p.pade_tol)
+                    greedy_criterion=["max", "min"][p.greedy_crit], real_margin=p.real_margin, pade_tol=p.pade_tol,
+                    real_set=["generic", "refined"][p.real_set], n_core=p.n_core, n_val=p.n_val, delta_c=p.delta_c,
+                    delta_v=p.delta_v)
 
 
 def test_gauss_legendre_grid(ctx):
