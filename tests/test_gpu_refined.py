@@ -61,7 +61,9 @@ def test_refined_cdwac_sigma_and_qp_small(ctx):
 
 def test_refined_two_states_ragged(ctx):
     spec = inputs.custom_system(70, 9, 200, seed=8, n_core=2, states=(0, 1), core_scale=0.3)
-    p = cdwac.Params.refined(8, 13, delta_c=0.4, delta_v=0.7, n_imag=40, pade_M=48)
+    # CD-WAC(12, 12, 40) with M = 40: a setting whose continuation is well conditioned on much of the grid (with
+    # M = 48 nearly every omega is ill conditioned, which leaves only the loose sensitivity-scaled bound)
+    p = cdwac.Params.refined(12, 12, n_imag=40, pade_M=40)
     omega = inputs.omega_grid(48)
     r = _wac_case(ctx, spec, p, omega)
     for s in range(2):
@@ -69,7 +71,10 @@ def test_refined_two_states_ragged(ctx):
         _assert_sigma(r["sig"][s], sig_rep, sens)
         assert r["qs"][s] == q.status
         if q.status < 2:
-            assert abs(r["e"][s] - q.e_qp) < HA_TOL
+            # the fixed point stops once |e_k+1 - e_k| < 1e-7 Ha, which fixes e_QP only to 1e-7 |s| / (1 - |s|)
+            # with s = dSigma/domega = 1 - 1/Z on each side (here Z ~ 0.5: a slow, oscillating iteration)
+            slope = abs(1.0 - 1.0 / q.Z)
+            assert abs(r["e"][s] - q.e_qp) < max(HA_TOL, 2e-7 * slope / (1.0 - slope))
 
 
 @pytest.mark.parametrize("bad", [dict(n_real=39), dict(delta_c=-0.1), dict(delta_v=float("nan")), dict(n_core=-1,
