@@ -594,3 +594,91 @@ def run_cd(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None
             res["sigma"] = np.array([sig(w) for w in omega_grid])
         out["states"].append(res)
     return out
+
+
+# ---------------------------------------------------------------------------------------------------------
+# Eigenvalue self-consistency beyond G0W0 (Sec. 5.4): evGW0 and evGW
+# ---------------------------------------------------------------------------------------------------------
+
+
+def sigma_I_subtracted(W_imag_s, W_zero_s, eps, n_occ, xi, wxi, omega, eta):
+    """I_n(omega) of Eq. In_term with W_nm(0) taken out of the quadrature and integrated in closed form.
+
+    The folded kernel K(a, xi) = 1/(a + i xi) + 1/(a - i xi) = 2a / (a^2 + xi^2), a = omega - eps_m - i eta s_m,
+    has width |omega - eps_m|: once omega comes closer to eps_m than the first quadrature nodes (every evGW cycle
+    evaluates Sigma_n next to its own updated eps_n) the rule misses most of it.  Its integral over [0, inf) is
+    pi sgn(omega - eps_m) (0 at omega = eps_m, the theta(0) = 1/2 reading), so
+    I_n = 1/(2 pi) sum_m [pi sgn(omega - eps_m) W_nm(0) + sum_k w_k (W_nm(i xi_k) - W_nm(0)) K(a_m, xi_k)];
+    the remaining integrand vanishes like xi^2 at the origin, where W is even and smooth.
+    W_zero_s [N_b] holds W_nm(0)."""
+    a = omega - eps - 1j * eta * occupation_sign(eps, n_occ)
+    kern = 1.0 / (a[None, :] + 1j * xi[:, None]) + 1.0 / (a[None, :] - 1j * xi[:, None])
+    closed = np.pi * np.sign(omega - eps) * W_zero_s
+    return (np.sum(closed) + np.sum(wxi[:, None] * (W_imag_s - W_zero_s[None, :]) * kern)) / (2.0 * np.pi)
+
+
+def _ev_tables(B, eps_W, On, n_occ, states, params, method, xi):
+    """W-side tables of one cycle, built from the energies eps_W: transition energies, W(i xi), W(0) and, for
+    CD-WAC, the near-real references (placed from eps_W) and the greedy Thiele fits."""
+    D = transition_energies(eps_W, n_occ)
+    t = {"D": D}
+    if method == "pole":
+        return t
+    t["W_imag"] = w_imag_table(B, D, On, xi)
+    t["W_zero"] = w_imag_table(B, D, On, np.zeros(1))[:, 0, :]
+    if method == "cdwac":
+        zr = reference_points(eps_W, n_occ, eps_W[list(states)], params)
+        Wre = w_complex_table(B, D, On, zr, np.arange(n_occ)) if len(zr) else None
+        t["models"] = [fit_wac(t["W_imag"][s], Wre[s] if len(zr) else np.zeros((0, n_occ), complex), xi, zr, n_occ,
+                               params.pade_M, params.greedy_first, params.greedy_criterion, params.pade_tol)
+                       for s in range(len(states))]
+    return t
+
+
+def run_evgw(B, On, eps, n_occ, states, params: Params, omega_grid, mode="evGW0", method="cdwac", shifts=None,
+             cycle_tol=1e-6, max_cycles=30):
+    """evGW0 or evGW (Sec. 5.4) for the requested states.
+
+    Cycle k solves e_n = eps_n + shift_n + Re Sigma^c_n(e_n) (Eq. qp_eq, eps_n the KS energy) with G built from
+    eps_G: the KS energies whose requested-state entries carry the QP energies of cycle k-1 (eps_G = eps in cycle
+    1, which is G0W0); every other orbital keeps its KS energy.
+      evGW0: W from the KS transition energies, built (and, for CD-WAC, fitted) once for all cycles.
+      evGW:  W from the transition energies of eps_G, rebuilt every cycle together with the near-real references
+             (placed from eps_G) and the Thiele fits.
+    method: "cdwac" (continued residue term), "cd" (W built at every residue) or "pole" (sum over poles of
+    Eq. sigma_pole, exact for both modes).  The I term is sigma_I_subtracted.  Ends when every requested state
+    moves by less than cycle_tol between two cycles (converged), when a QP equation has no solution (status 2) or
+    after max_cycles."""
+    if mode not in ("evGW0", "evGW") or method not in ("cdwac", "cd", "pole"):
+        raise ValueError("mode evGW0|evGW, method cdwac|cd|pole")
+    xi, wxi = imaginary_grid(params.n_imag, params.omega0)
+    epsG = np.array(eps, dtype=float)
+    idx = list(states)
+    tabs = None
+    history = []
+    for cycle in range(1, max_cycles + 1):
+        if tabs is None or mode == "evGW":
+            tabs = _ev_tables(B, epsG if mode == "evGW" else np.asarray(eps, float), On, n_occ, idx, params, method,
+                              xi)
+        res = []
+        for s, n in enumerate(idx):
+            if method == "pole":
+                sig = lambda w, s=s, G=epsG.copy(): sigma_c_pole_sum(B, tabs["D"], On[s], G, n_occ, w, params.eta)
+            elif method == "cd":
+                sig = lambda w, s=s, G=epsG.copy(): (sigma_R_cd(B, tabs["D"], On[s], G, n_occ, w, params.eta) -
+                                                     sigma_I_subtracted(tabs["W_imag"][s], tabs["W_zero"][s], G,
+                                                                        n_occ, xi, wxi, w, params.eta))
+            else:
+                sig = lambda w, s=s, G=epsG.copy(): (sigma_R_wac(tabs["models"][s], G, n_occ, w, params.eta) -
+                                                     sigma_I_subtracted(tabs["W_imag"][s], tabs["W_zero"][s], G,
+                                                                        n_occ, xi, wxi, w, params.eta))
+            sh = 0.0 if shifts is None else shifts[s]
+            res.append(qp_solve(sig, eps[n], sh, omega_grid, upper=epsG[n_occ] if method == "cdwac" else np.inf))
+        e = np.array([q.e_qp for q in res])
+        history.append(e)
+        if any(q.status == 2 for q in res):
+            return {"e_qp": e, "qp": res, "cycles": cycle, "status": 2, "history": history}
+        if np.max(np.abs(e - epsG[idx])) < cycle_tol:
+            return {"e_qp": e, "qp": res, "cycles": cycle, "status": 0, "history": history}
+        epsG[idx] = e
+    return {"e_qp": e, "qp": res, "cycles": max_cycles, "status": 1, "history": history}

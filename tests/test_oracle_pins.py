@@ -360,3 +360,95 @@ def test_spectral_function_sum_rule_one_pole_self_energy():
     z1 = (w1 - b) / (w1 - w2)
     near1 = np.abs(w - w1) < 0.2
     assert abs(np.trapezoid(A[near1], w[near1]) - z1) < 2e-2
+
+
+# ---- eigenvalue self-consistency, evGW0 and evGW (Sec. 5.4) ------------------------------------------------------
+
+def _one_transition():
+    # n_basis 2, n_occ 1, N_aux 1: W_0m(z) = 4 o_0m^2 b^2 D / (z^2 - Omega^2), Omega^2 = D^2 + 4 b^2 D, so
+    # Eq. sigma_pole has one pole per orbital with weights (w_0m)^2 = 2 o_0m^2 b^2 D / Omega
+    b, o00, o01, e0, e1 = 0.7, 0.5, 0.8, -10.0, 0.6
+    return b, o00, o01, e0, e1, np.array([[b]]), np.array([[[o00, o01]]]), np.array([e0, e1])
+
+
+def _weights(b, o00, o01, d):
+    om = math.sqrt(d * d + 4 * b * b * d)
+    return om, 2 * o00 ** 2 * b ** 2 * d / om, 2 * o01 ** 2 * b ** 2 * d / om
+
+
+@pytest.mark.parametrize("method", ["pole", "cd", "cdwac"])
+def test_evgw0_one_transition_closed_form(method):
+    # evGW0: W stays at the KS transition D = e1 - e0, G carries eps_G = (e, e1); at self-consistency
+    # e = e0 + A / (e - e + Omega) + B / (e - e1 - Omega), a quadratic whose root below e1 + Omega is the answer
+    b, o00, o01, e0, e1, B, On, eps = _one_transition()
+    om, A, Bw = _weights(b, o00, o01, e1 - e0)
+    c, d = e0 + A / om, e1 + om
+    expect = 0.5 * ((c + d) - math.sqrt((c - d) ** 2 + 4 * Bw))
+    P = o.Params(n_imag=100, n_real=8, pade_M=2, eta=1e-8)
+    r = o.run_evgw(B, On, eps, 1, [0], P, np.linspace(-11, -9.5, 64), mode="evGW0", method=method)
+    assert r["status"] == 0 and r["cycles"] > 1
+    assert abs(r["e_qp"][0] - expect) < 1e-9
+
+
+@pytest.mark.parametrize("method", ["pole", "cd", "cdwac"])
+def test_evgw_one_transition_root(method):
+    # evGW: W follows eps_G too, D = e1 - e; the fixed point is the root of
+    # g(e) = e - e0 - A(e) / Omega(e) - B(e) / (e - e1 - Omega(e)) near e0 (bracketed and bisected)
+    from scipy.optimize import brentq
+    b, o00, o01, e0, e1, B, On, eps = _one_transition()
+
+    def g(e):
+        om, A, Bw = _weights(b, o00, o01, e1 - e)
+        return e - e0 - A / om - Bw / (e - e1 - om)
+
+    expect = brentq(g, e0 - 0.5, e0 + 0.1, xtol=1e-14)
+    P = o.Params(n_imag=100, n_real=8, pade_M=2, eta=1e-8)
+    r = o.run_evgw(B, On, eps, 1, [0], P, np.linspace(-11, -9.5, 64), mode="evGW", method=method)
+    assert r["status"] == 0
+    assert abs(r["e_qp"][0] - expect) < 1e-9
+
+
+def test_evgw_cd_and_cdwac_match_the_sum_over_poles():
+    # 16 orbitals, 39 transitions: the exact evGW0 / evGW fixed points from Eq. sigma_pole against plain CD and
+    # CD-WAC with the subtracted I term; self-consistency moves the core level by 0.3-0.7 mHa from G0W0
+    spec = inputs.custom_system(16, 3, 40, seed=3, n_core=1, states=(0,), core_scale=0.3, valence=(-1.1, -0.3),
+                                virtual=(0.02, 2.0))
+    eps = inputs.eigenvalues(spec)
+    B, On = inputs.build_B(spec), inputs.build_On(spec)
+    grid = inputs.omega_grid(64)
+    P = o.Params(n_imag=60, n_real=20, pade_M=40)
+    ref = {}
+    for mode in ("evGW0", "evGW"):
+        r = {m: o.run_evgw(B, On, eps, 3, [0], P, grid, mode=mode, method=m) for m in ("pole", "cd", "cdwac")}
+        assert all(v["status"] == 0 for v in r.values())
+        e = r["pole"]["e_qp"][0]
+        assert abs(r["cd"]["e_qp"][0] - e) < 2e-8 and abs(r["cdwac"]["e_qp"][0] - e) < 2e-8
+        # cycle 1 is G0W0 (G and W from the KS energies)
+        D = o.transition_energies(eps, 3)
+        g0w0 = o.qp_solve(lambda w: o.sigma_c_pole_sum(B, D, On[0], eps, 3, w, P.eta), eps[0], 0.0, grid)
+        assert abs(r["pole"]["history"][0][0] - g0w0.e_qp) < 1e-12
+        assert abs(e - g0w0.e_qp) > 1e-4
+        # the answer is self-consistent: G built with eps_G[n] = e reproduces e
+        G = eps.copy()
+        G[0] = e
+        Dm = o.transition_energies(G if mode == "evGW" else eps, 3)
+        assert abs(eps[0] + o.sigma_c_pole_sum(B, Dm, On[0], G, 3, e, P.eta).real - e) < 1e-6
+        ref[mode] = e
+    assert abs(ref["evGW"] - ref["evGW0"]) > 1e-4
+
+
+def test_subtracted_i_term_equals_quadrature_away_from_eps_m(small):
+    # far from every eps_m both forms of Eq. In_term agree; 1.6 mHa from eps_n the plain rule misses the narrow
+    # Lorentzian that the closed-form part carries (against the sum over poles)
+    s = small
+    Wz = o.w_imag_table(s["B"], s["D"], s["On"], np.zeros(1))[0, 0]
+    args = (s["eps"], 5, s["xi"], s["wxi"])
+    for w in (-10.9, -10.3):
+        plain = o.sigma_I(s["Wim"][0], *args, w, 1e-3)
+        assert abs(plain - o.sigma_I_subtracted(s["Wim"][0], Wz, *args, w, 1e-3)) < 1e-10
+    w = s["eps"][0] + 0.0016
+    exact = o.sigma_c_pole_sum(s["B"], s["D"], s["On"][0], s["eps"], 5, w, 1e-3)
+    R = o.sigma_R_cd(s["B"], s["D"], s["On"][0], s["eps"], 5, w, 1e-3)
+    sub = R - o.sigma_I_subtracted(s["Wim"][0], Wz, *args, w, 1e-3)
+    plain = R - o.sigma_I(s["Wim"][0], *args, w, 1e-3)
+    assert abs(sub.real - exact.real) < 1e-10 < 1e-7 < abs(plain.real - exact.real)
