@@ -213,6 +213,28 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
+/* Eigenvalue self-consistency beyond G0W0 (Sec. 5.4) for the requested states, CD-WAC.
+ * Cycle k solves the QP equation e_n = eps_n + shift_n + Re Sigma^c_n(e_n) (eps_n: sys->eps) of every requested
+ * state with G built from eps_G: sys->eps with the requested entries replaced by the QP energies of cycle k-1
+ * (cycle 1 is G0W0); every other orbital keeps its energy.
+ *   mode CDWAC_EVGW0  W (imaginary grid and near-real references) and the Thiele fits from sys->eps, built once.
+ *        CDWAC_EVGW   W, the near-real references (placed from eps_G) and the fits rebuilt every cycle from eps_G.
+ * The I term carries W_nm(0) in closed form (its Lorentzian integrates to sgn(omega - eps_m) pi / 2 whatever the
+ * grid), since at self-consistency Sigma_n is evaluated at its own G energy, closer to it than the grid resolves.
+ *   shift       [n_states]  in (device, may be NULL): Sigma^x_n - v^xc_n
+ *   omega       [n_grid]    in (device): bracketing grid of the QP solver, as in cdwac_qp_solve (n_grid >= 2)
+ *   cycle_tol               self-consistency reached when no requested state moves by cycle_tol (Ha) or more
+ *   max_cycles              at least 1
+ *   e_qp, Z, qp_status [n_states] out (device): the last cycle's QP solutions (qp_status as cdwac_qp_solve)
+ *   cycles      [1]         out (HOST int): cycles run
+ * Host-driven: the call synchronises `stream` once per cycle.  Returns CDWAC_ERR_QP_NOT_CONVERGED when a QP
+ * equation has no solution or max_cycles pass without self-consistency (outputs hold the last cycle), CDWAC_ERR_ARG
+ * when an updated level crosses the Fermi level.  Allocates its tables (eps_G, W, W(0), fits) for the call. */
+typedef enum { CDWAC_EVGW0 = 0, CDWAC_EVGW = 1 } cdwac_ev_mode;
+cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode,
+                        const double* shift, const double* omega, int n_grid, double cycle_tol, int max_cycles,
+                        double* e_qp, double* Z, int* qp_status, int* cycles, void* stream);
+
 /* Diagonal spectral function (Sec. 5.5): A_nn(omega_j) = |Im[(omega_j - eps_n - shift_n - Sigma^c_n(omega_j))^-1]|
  * / pi, the imaginary part of the Green's function (normalised so that one quasiparticle pole carries weight one).
  * Sigma^c as in cdwac_sigma: CD-WAC from the continued fractions (pade != NULL) or plain CD (pade == NULL), which

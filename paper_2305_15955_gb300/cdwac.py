@@ -25,12 +25,13 @@ F64, F32 = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 LDLT_FP64, LDLT_EMULATED = 0, 1
 REAL_GENERIC, REAL_REFINED = 0, 1
+EVGW0, EVGW = 0, 1
 MAX_M = 256
 EXPORTED = ["cdwac_create", "cdwac_destroy", "cdwac_last_error", "cdwac_default_params", "cdwac_sync_status",
             "cdwac_scratch_bytes", "cdwac_build_W_imag", "cdwac_fit_pade", "cdwac_sigma", "cdwac_qp_solve",
             "cdwac_profile_enable", "cdwac_profile_read", "cdwac_launch_count", "cdwac_build_W_imag_noalloc",
             "cdwac_batch_run", "cdwac_mlp_features", "cdwac_mlp_loss_grad", "cdwac_mlp_adam", "cdwac_mlp_poles",
-            "cdwac_sigma_poles", "cdwac_qp_solve_poles"]
+            "cdwac_sigma_poles", "cdwac_qp_solve_poles", "cdwac_spectral", "cdwac_ldlt_factor", "cdwac_evgw"]
 MLP_IN, MLP_HIDDEN, MLP_POLES = 32, 256, 8
 MLP_NPARAMS = 32 * 256 + 256 + 2 * (256 * 256 + 256) + 256 * 16 + 16
 BATCH_GRAPH, BATCH_AUTOTUNE = 1, 2
@@ -114,6 +115,8 @@ def load():
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
     lib.cdwac_ldlt_factor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     lib.cdwac_spectral.argtypes = [P, sysp, prmp, P, P, P, padep, P, P, ctypes.c_int, P, P, P]
+    lib.cdwac_evgw.argtypes = [P, sysp, prmp, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P,
+                               P, ctypes.POINTER(ctypes.c_int), P]
     lib.cdwac_mlp_features.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                        ctypes.c_int, P, P, P, P, P]
     lib.cdwac_mlp_loss_grad.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
@@ -335,6 +338,26 @@ class Context:
 
     def _dev(self):
         return torch.device("cuda", self.device)
+
+    def evgw(self, system: System, params: Params, mode, omega_grid, shift=None, cycle_tol=1e-6, max_cycles=30):
+        """cdwac_evgw: (e_qp, Z, qp_status [n_states] on the device, cycles, status).  status is OK or
+        ERR_QP_NOT_CONVERGED (no solution in a cycle, or max_cycles without self-consistency); other errors raise."""
+        dev = self._dev()
+        grid = torch.as_tensor(omega_grid, dtype=torch.float64).to(dev).contiguous()
+        sh = None if shift is None else torch.as_tensor(shift, dtype=torch.float64).to(dev).contiguous()
+        ns = system.n_states
+        e = torch.empty(ns, dtype=torch.float64, device=dev)
+        Z = torch.empty_like(e)
+        qs = torch.empty(ns, dtype=torch.int32, device=dev)
+        cycles = ctypes.c_int(0)
+        p = params.c()
+        st = self.lib.cdwac_evgw(self.h, ctypes.byref(system.c), ctypes.byref(p), int(mode), _ptr(sh), _ptr(grid),
+                                 int(grid.numel()), float(cycle_tol), int(max_cycles), _ptr(e), _ptr(Z), _ptr(qs),
+                                 ctypes.byref(cycles), self._stream())
+        if st not in (OK, ERR_QP_NOT_CONVERGED):
+            self._check(st)
+        self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
+        return e, Z, qs, cycles.value, st
 
     def spectral(self, system: System, params: Params, xi, wxi, W_imag, pade: PadeModel | None, omega, shift=None,
                  sync=True):

@@ -432,13 +432,10 @@ static cdwac_status imag_freqs(cdwac_ctx* lc, const cdwac_system* sys, const cdw
   return CDWAC_OK;
 }
 
-cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
-                                double* wxi, double* W_imag, void* stream) {
-  cdwac_status rc = check_system(ctx, sys, prm);
-  if (rc) return rc;
-  if (!xi || !wxi || !W_imag) return set_error(ctx, CDWAC_ERR_ARG, "null output");
-  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-  cudaStream_t st = (cudaStream_t)stream;
+// W_nm(i xi_k) at the prm->n_imag imaginary frequencies xi [device] into W [n_states][n_imag][n_basis].
+static cdwac_status build_W_freqs(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
+                                  double* W_imag, cudaStream_t st) {
+  cdwac_status rc;
   const int n = sys->n_aux, nb = sys->n_basis, n_occ = sys->n_occ, n_virt = nb - n_occ;
   const long n_ov = (long)n_occ * n_virt;
   const bool mixed = prm->precision == CDWAC_PREC_MIXED;
@@ -457,7 +454,6 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
   void* tc_shared = mixed ? ar.take<char>(tc_pi_shared_bytes(n, n_ov)) : nullptr;
   {
     ProfScope ps(ctx, PROF_GRID, st);
-    if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
     if ((rc = launch_transition_energies(ctx, sys->eps, n_occ, n_virt, D, st))) return rc;
   }
   if (mixed) {
@@ -479,6 +475,20 @@ cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const c
     if (rc) return set_error(ctx, rc, "lane %d: %s", l, ctx->lanes[l]->last_error.c_str());
   }
   return join_lanes(ctx, L, st);
+}
+
+cdwac_status cdwac_build_W_imag(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, double* xi,
+                                double* wxi, double* W_imag, void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if (!xi || !wxi || !W_imag) return set_error(ctx, CDWAC_ERR_ARG, "null output");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  {
+    ProfScope ps(ctx, PROF_GRID, st);
+    if ((rc = launch_gauss_legendre(ctx, prm->n_imag, prm->omega0, xi, wxi, st))) return rc;
+  }
+  return build_W_freqs(ctx, sys, prm, xi, W_imag, st);
 }
 
 struct RealBufs {
@@ -835,6 +845,117 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
 }
 
 }  // extern "C"
+
+// ---- eigenvalue self-consistency beyond G0W0 (evGW0, evGW) -------------------------------------------------
+
+namespace {
+struct EvBufs {
+  double *epsG, *xi, *wxi, *W, *W0, *zero;
+  cplx *pa, *pz2;
+  int *nodes, *used, *iters;
+};
+
+void carve_ev(Arena& a, EvBufs& b, int nb, int ns, int ni, int n_occ, int M) {
+  b.epsG = a.take<double>(nb);
+  b.xi = a.take<double>(ni);
+  b.wxi = a.take<double>(ni);
+  b.W = a.take<double>((size_t)ns * ni * nb);
+  b.W0 = a.take<double>((size_t)ns * nb);
+  b.zero = a.take<double>(1);
+  b.pa = a.take<cplx>((size_t)ns * n_occ * M);
+  b.pz2 = a.take<cplx>((size_t)ns * n_occ * M);
+  b.nodes = a.take<int>((size_t)ns * n_occ * M);
+  b.used = a.take<int>((size_t)ns * n_occ);
+  b.iters = a.take<int>(ns);
+}
+
+struct DeviceFree {
+  void* p;
+  ~DeviceFree() {
+    if (p) cudaFree(p);
+  }
+};
+}  // namespace
+
+extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode,
+                                   const double* shift, const double* omega, int n_grid, double cycle_tol,
+                                   int max_cycles, double* e_qp, double* Z, int* qp_status, int* cycles,
+                                   void* stream) {
+  cdwac_status rc = check_system(ctx, sys, prm);
+  if (rc) return rc;
+  if ((mode != CDWAC_EVGW0 && mode != CDWAC_EVGW) || !omega || n_grid < 2 || !e_qp || !Z || !qp_status ||
+      !cycles || !(cycle_tol > 0) || max_cycles < 1)
+    return set_error(ctx, CDWAC_ERR_ARG, "bad evgw args");
+  CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int ns = sys->n_states, nb = sys->n_basis, n_occ = sys->n_occ, ni = prm->n_imag, M = prm->pade_M;
+  // tables kept across the cycles (the W builds use the context scratch for their own work)
+  Arena dry(nullptr);
+  EvBufs b;
+  carve_ev(dry, b, nb, ns, ni, n_occ, M);
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, dry.off + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(ctx, CDWAC_ERR_OOM, "evgw tables (%zu bytes): %s", dry.off, cudaGetErrorString(e));
+  }
+  DeviceFree guard{buf};
+  Arena ar(buf);
+  carve_ev(ar, b, nb, ns, ni, n_occ, M);
+  std::vector<double> hG(nb), he(ns);
+  std::vector<int> hs(ns), hst(ns);
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(b.epsG, sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemsetAsync(b.zero, 0, sizeof(double), st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sys->states, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  for (int s = 0; s < ns; ++s)
+    if (hs[s] < 0 || hs[s] >= nb) return set_error(ctx, CDWAC_ERR_ARG, "state index %d out of range", hs[s]);
+  cdwac_system sysG = *sys;   // G from eps_G
+  sysG.eps = b.epsG;
+  cdwac_pade pade{ns, n_occ, M, reinterpret_cast<double*>(b.pa), reinterpret_cast<double*>(b.pz2), b.nodes, b.used};
+  cdwac_params p0 = *prm;     // W(0): one frequency at xi = 0
+  p0.n_imag = 1;
+  int cyc = 1, outcome = 0;   // 1 self-consistent, 2 a QP equation without solution
+  for (; cyc <= max_cycles; ++cyc) {
+    if (cyc == 1 || mode == CDWAC_EVGW) {
+      // evGW0 keeps W, the near-real references and the fits of the KS energies; evGW rebuilds them from eps_G
+      const cdwac_system* sw = mode == CDWAC_EVGW ? &sysG : sys;
+      if ((rc = cdwac_build_W_imag(ctx, sw, prm, b.xi, b.wxi, b.W, st))) return rc;
+      if ((rc = build_W_freqs(ctx, sw, &p0, b.zero, b.W0, st))) return rc;
+      if ((rc = cdwac_fit_pade(ctx, sw, prm, b.xi, b.W, nullptr, nullptr, &pade, st))) return rc;
+    }
+    {
+      ProfScope ps(ctx, PROF_QP, st);
+      if ((rc = launch_qp_wac(ctx, &sysG, prm, b.xi, b.wxi, b.W, &pade, shift, omega, n_grid, 1e-7, 100, e_qp, Z,
+                              b.iters, qp_status, st, b.W0, sys->eps)))
+        return rc;
+    }
+    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(he.data(), e_qp, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hst.data(), qp_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+    CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    double dmax = 0.0;
+    for (int s = 0; s < ns; ++s) {
+      if (hst[s] == 2) outcome = 2;
+      dmax = fmax(dmax, fabs(he[s] - hG[hs[s]]));
+    }
+    if (outcome == 2) break;
+    if (dmax < cycle_tol) {
+      outcome = 1;
+      break;
+    }
+    for (int s = 0; s < ns; ++s) hG[hs[s]] = he[s];
+    if (!(hG[n_occ - 1] < hG[n_occ]))
+      return set_error(ctx, CDWAC_ERR_ARG, "evgw: an updated level crossed the Fermi level (cycle %d)", cyc);
+    if ((rc = launch_scatter_states(ctx, b.epsG, sys->states, e_qp, ns, st))) return rc;
+  }
+  *cycles = cyc > max_cycles ? max_cycles : cyc;
+  CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (outcome == 1) return CDWAC_OK;
+  return set_error(ctx, CDWAC_ERR_QP_NOT_CONVERGED, outcome == 2 ? "evgw: a QP equation has no solution (cycle %d)"
+                                                                  : "evgw: not self-consistent after %d cycles",
+                   *cycles);
+}
 
 // ---- learned continuation in the residue term -------------------------------------------------------------
 

@@ -283,7 +283,13 @@ cdwac_status launch_qp_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwa
                              const double* wxi, const double* W_imag, const double* poles, const double* shift,
                              const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                              int* iters, int* qp_status, cudaStream_t st);
+// W_zero [n_states][n_basis] (optional): the I term's W(0) part in closed form; eps_qp (optional): the energies
+// eps_n of the QP equation when sys->eps holds those of G (evGW), the fixed point starting from sys->eps.
 cdwac_status launch_qp_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
                            const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
-                           int* iters, int* qp_status, cudaStream_t st);
+                           int* iters, int* qp_status, cudaStream_t st, const double* W_zero = nullptr,
+                           const double* eps_qp = nullptr);
+// eps[states[i]] = e[i]
+cdwac_status launch_scatter_states(cdwac_ctx* ctx, double* eps, const int* states, const double* e, int n,
+                                   cudaStream_t st);

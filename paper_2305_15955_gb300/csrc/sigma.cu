@@ -33,6 +33,10 @@ struct SigmaArgs {
   int M_cap;
   // learned continuation (may be null): [n_states][n_occ][CDWAC_MLP_POLES][2] (Omega, residue)
   const double* poles;
+  // W_nm(0) [n_states][n_basis] (may be null): the I term's xi -> 0 part integrated in closed form
+  const double* W_zero;
+  // energies eps_n of the QP equation (may be null: eps); eps then holds the energies of G
+  const double* eps_qp;
 };
 
 __device__ inline double theta(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? 0.0 : 0.5); }
@@ -60,20 +64,26 @@ __device__ inline cplx block_sum(cplx v, cplx* red) {
 }
 
 // This thread's share of I_n(omega) for state s (sum over m strided by the block, all k).
+// With W_zero: I_n = sum_m [sgn(omega - eps_m) W_nm(0) / 2 + 1/pi sum_k wxi_k (W_nm(i xi_k) - W_nm(0)) a/(a^2+xi^2)]:
+// the Lorentzian of width |omega - eps_m| integrates to pi/2 sgn(omega - eps_m) over [0, inf) whatever the grid,
+// and what is left vanishes like xi^2 at the origin (needed when omega sits next to eps_m, as at evGW
+// self-consistency).
 __device__ inline cplx partial_I(const SigmaArgs& A, int s, double omega) {
-  const double ef = 0.5 * (A.eps[A.n_occ - 1] + A.eps[A.n_occ]);
-  (void)ef;
   const double* W = A.W_imag + (long)s * A.n_imag * A.n_basis;
+  const double* W0 = A.W_zero ? A.W_zero + (long)s * A.n_basis : nullptr;
   cplx acc = mkc(0.0, 0.0);
+  double closed = 0.0;
   for (int m = threadIdx.x; m < A.n_basis; m += blockDim.x) {
     const double al = omega - A.eps[m];
     const double be = -A.eta * (m < A.n_occ ? 1.0 : -1.0);
+    const double w0 = W0 ? W0[m] : 0.0;
+    closed += al > 0.0 ? 0.5 * w0 : (al < 0.0 ? -0.5 * w0 : 0.0);
     if (!A.mixed) {
       double sr = 0.0, si = 0.0;
       for (int k = 0; k < A.n_imag; ++k) {
         const double x = A.xi[k];
         const double u = al * al - be * be + x * x, v = 2.0 * al * be;
-        const double c = A.wxi[k] * W[(long)k * A.n_basis + m] / (u * u + v * v);
+        const double c = A.wxi[k] * (W[(long)k * A.n_basis + m] - w0) / (u * u + v * v);
         sr += c * (al * u + be * v);
         si += c * (be * u - al * v);
       }
@@ -85,7 +95,7 @@ __device__ inline cplx partial_I(const SigmaArgs& A, int s, double omega) {
       for (int k = 0; k < A.n_imag; ++k) {
         const float x = (float)A.xi[k];
         const float u = alf * alf - bef * bef + x * x, v = 2.f * alf * bef;
-        const float c = (float)A.wxi[k] * (float)W[(long)k * A.n_basis + m] / (u * u + v * v);
+        const float c = (float)A.wxi[k] * (float)(W[(long)k * A.n_basis + m] - w0) / (u * u + v * v);
         sr += c * (alf * u + bef * v);
         si += c * (bef * u - alf * v);
       }
@@ -93,7 +103,7 @@ __device__ inline cplx partial_I(const SigmaArgs& A, int s, double omega) {
       acc.y += (double)si;
     }
   }
-  return mkc(acc.x * INV_PI, acc.y * INV_PI);
+  return mkc(acc.x * INV_PI + closed, acc.y * INV_PI);
 }
 
 // This thread's share of R_n(omega) from the continued fractions (occupied m).
@@ -163,7 +173,7 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
                                                          double* Zout, int* iters, int* qst, unsigned* status) {
   __shared__ cplx red[33];
   const int s = blockIdx.x;
-  const double en = A.eps[A.states[s]];
+  const double en = A.eps_qp ? A.eps_qp[A.states[s]] : A.eps[A.states[s]];
   const double sh = shift ? shift[s] : 0.0;
   const double h = 1e-5;
   auto resig = [&](double w) { return block_sigma(A, s, w, red, status, false).x; };
@@ -173,7 +183,7 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
     double d = (resig(e + h) - resig(e - h)) / (2.0 * h);
     return 1.0 / (1.0 - d);
   };
-  double e = en;
+  double e = A.eps[A.states[s]];     // the fixed point starts from the state's energy in G
   int it = 1;
   int conv = 0;
   double e_new = e;
@@ -262,7 +272,15 @@ SigmaArgs make_args(const cdwac_system* sys, const cdwac_params* prm, const doub
   A.n_used = pade ? pade->n_used : nullptr;
   A.M_cap = pade ? pade->M : 0;
   A.poles = nullptr;
+  A.W_zero = nullptr;
+  A.eps_qp = nullptr;
   return A;
+}
+
+__global__ void scatter_states_kernel(double* __restrict__ eps, const int* __restrict__ states,
+                                      const double* __restrict__ e, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) eps[states[i]] = e[i];
 }
 
 // Diagonal spectral function (Sec. 5.5): A = |Im[(omega - eps_n - shift_n - Sigma^c_n(omega))^-1]| / pi
@@ -310,8 +328,10 @@ cdwac_status launch_sigma_I_only(cdwac_ctx* ctx, const cdwac_system* sys, const 
 cdwac_status launch_qp_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                            const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* shift,
                            const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
-                           int* iters, int* qp_status, cudaStream_t st) {
+                           int* iters, int* qp_status, cudaStream_t st, const double* W_zero, const double* eps_qp) {
   SigmaArgs A = make_args(sys, prm, xi, wxi, W_imag, pade);
+  A.W_zero = W_zero;
+  A.eps_qp = eps_qp;
   qp_kernel<<<sys->n_states, SIG_THREADS, 0, st>>>(A, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters,
                                                      qp_status, ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
@@ -338,6 +358,14 @@ cdwac_status launch_qp_poles(cdwac_ctx* ctx, const cdwac_system* sys, const cdwa
   A.poles = poles;
   qp_kernel<<<sys->n_states, SIG_THREADS, 0, st>>>(A, shift, omega, n_grid, tol, max_iter, e_qp, Z, iters, qp_status,
                                                      ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+cdwac_status launch_scatter_states(cdwac_ctx* ctx, double* eps, const int* states, const double* e, int n,
+                                   cudaStream_t st) {
+  if (n <= 0) return CDWAC_OK;
+  scatter_states_kernel<<<ceil_div(n, 128), 128, 0, st>>>(eps, states, e, n);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }

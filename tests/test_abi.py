@@ -38,3 +38,6 @@ def test_default_params_and_errors_without_gpu():
     # null arguments are rejected on the host, before any CUDA call
     assert lib.cdwac_create(None, 0) == cdwac.ERR_ARG
     assert lib.cdwac_build_W_imag(None, None, None, None, None, None, None) == cdwac.ERR_ARG
+    cyc = ctypes.c_int(0)
+    assert lib.cdwac_evgw(None, None, None, 0, None, None, 0, 1e-6, 1, None, None, None, ctypes.byref(cyc),
+                          None) == cdwac.ERR_ARG
