@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--refined-map", action="store_true",
                     help="instead of the step: QP error of CD-WAC(N_core, N_val, N_Im) against plain CD over a grid "
                          "of refined-set sizes (one JSON line)")
+    ap.add_argument("--delta-c", type=float, default=0.5, help="refined core neighbourhood radius (Ha) of the map")
+    ap.add_argument("--delta-v", type=float, default=1.0, help="refined valence neighbourhood radius (Ha) of the map")
     return ap.parse_args()
 
 
@@ -554,8 +556,8 @@ def run_refined_map(args, rank, ws, dist):
     mae, mx, bad = ([[None] * len(sizes) for _ in sizes] for _ in range(3))
     for i, nc in enumerate(sizes):
         for j, nv in enumerate(sizes):
-            p = (cdwac.Params.refined(nc, nv, n_imag=ni, pade_M=min(cdwac.MAX_M, ni + nc + nv)) if nc + nv
-                 else base)
+            p = (cdwac.Params.refined(nc, nv, args.delta_c, args.delta_v, n_imag=ni,
+                                      pade_M=min(cdwac.MAX_M, ni + nc + nv)) if nc + nv else base)
             mae[i][j], mx[i][j], bad[i][j] = stats(errors(p))
     generic = {}
     for nr in (10, 20, 40, 80):
@@ -566,7 +568,7 @@ def run_refined_map(args, rank, ws, dist):
             "config": {"workload": "8 small systems: N_basis=40 (1 core at -10.6 Ha, 4 valence in [-1.1,-0.3], 35 "
                                    "virtual log-spaced in [0.02,2.0]), N_aux=120, core entries x0.3, seeds 0-7; "
                                    "core state n=0; 128 omega in [-11,-10] Ha", "n_imag": ni,
-                       "delta_c_Ha": 0.5, "delta_v_Ha": 1.0, "pade_M": "N_core + N_val + N_Im"},
+                       "delta_c_Ha": args.delta_c, "delta_v_Ha": args.delta_v, "pade_M": "N_core + N_val + N_Im"},
             "sizes": list(sizes), "rows": "N_core", "cols": "N_val", "mae_meV": mae, "max_meV": mx,
             "not_converged": bad, "generic": generic, "plain_cd_qp_s": t_cd,
             "plain_cd_qp_status": [s[5] for s in systems]}
