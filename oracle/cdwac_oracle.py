@@ -17,12 +17,18 @@ Conventions (readings of points the paper leaves open):
     Pi(z) = 2 sum_ia O^ia [1/(z - D_ia) - 1/(z + D_ia)] O^ia, an even function of z;
   * greedy Thiele: the first node maximises |W|, every later node maximises the L1 error
     |Re(T - W)| + |Im(T - W)| of the current convergent over the remaining nodes; ties go to the lowest
-    candidate index; a node whose reciprocal difference is not finite ends the fit (breakdown).
+    candidate index; a node whose reciprocal difference is not finite ends the fit (breakdown);
+  * near-real references (Sec. 3.3): one set per system, centres taken at omega = eps_n of the requested states;
+    refined core centres |eps_n' - eps_n|, valence centres |eps_F - eps_n|, neighbourhoods cut at Re z = 0;
+  * evGW0 / evGW (Sec. 5.4): the requested states' QP energies replace their entries in G (and in W's transition
+    energies for evGW), other orbitals keep their KS energies; the I term takes W_nm(0) out of the quadrature and
+    integrates its part in closed form, because Sigma_n is then evaluated at its own G energy.
 
 Parity pins (tests/test_oracle_pins.py): the sum-over-poles self-energy of Eq. sigma_pole from a full RPA
 diagonalisation, the closed-form one-pole system, Gauss-Legendre exactness and known integrals,
-Thiele interpolation and one-pole exactness, invariants of Pi, Lambda and W.  The CD-WAC continuation error
-itself has no exact pin: it is a measured quantity of the method.
+Thiele interpolation and one-pole exactness, invariants of Pi, Lambda and W, a hand-worked refined reference set,
+closed-form one-transition evGW0 / evGW fixed points.  The CD-WAC continuation error itself has no exact pin: it
+is a measured quantity of the method.
 """
 from __future__ import annotations
 
