@@ -869,10 +869,15 @@ void carve_ev(Arena& a, EvBufs& b, int nb, int ns, int ni, int n_occ, int M) {
   b.iters = a.take<int>(ns);
 }
 
-struct DeviceFree {
+// Frees a call's own device tables once the work queued on its stream (lanes and side streams are joined back to
+// it before each internal call returns) has finished, on every return path.
+struct StreamFree {
   void* p;
-  ~DeviceFree() {
-    if (p) cudaFree(p);
+  cudaStream_t st;
+  ~StreamFree() {
+    if (!p) return;
+    cudaStreamSynchronize(st);
+    cudaFree(p);
   }
 };
 }  // namespace
@@ -899,7 +904,7 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
     cudaGetLastError();
     return set_error(ctx, CDWAC_ERR_OOM, "evgw tables (%zu bytes): %s", dry.off, cudaGetErrorString(e));
   }
-  DeviceFree guard{buf};
+  StreamFree guard{buf, st};
   Arena ar(buf);
   carve_ev(ar, b, nb, ns, ni, n_occ, M);
   std::vector<double> hG(nb), he(ns);
@@ -945,7 +950,10 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
       break;
     }
     for (int s = 0; s < ns; ++s) hG[hs[s]] = he[s];
-    if (!(hG[n_occ - 1] < hG[n_occ]))
+    // every transition energy eps_a - eps_i must stay positive
+    const double top_occ = *std::max_element(hG.begin(), hG.begin() + n_occ);
+    const double low_virt = *std::min_element(hG.begin() + n_occ, hG.end());
+    if (!(top_occ < low_virt))
       return set_error(ctx, CDWAC_ERR_ARG, "evgw: an updated level crossed the Fermi level (cycle %d)", cyc);
     if ((rc = launch_scatter_states(ctx, b.epsG, sys->states, e_qp, ns, st))) return rc;
   }
