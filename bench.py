@@ -50,7 +50,7 @@ def parse():
                     help="instead of the step: QP error of CD-WAC(N_core, N_val, N_Im) against plain CD over a grid "
                          "of refined-set sizes (one JSON line)")
     ap.add_argument("--delta-c", type=float, default=0.5, help="refined core neighbourhood radius (Ha) of the map")
-    ap.add_argument("--delta-v", type=float, default=1.0, help="refined valence neighbourhood radius (Ha) of the map")
+    ap.add_argument("--delta-v", type=float, default=0.5, help="refined valence neighbourhood radius (Ha) of the map")
     return ap.parse_args()
 
 
@@ -510,8 +510,8 @@ def run_refined_map(args, rank, ws, dist):
     of the reference-set calibration of Sec. 5.1 (an MAE over a set of core levels).  Eight seeded systems of the
     small recipe (N_basis 40: one core level at -10.6 Ha, 4 valence levels in [-1.1, -0.3], 35 virtuals log-spaced
     in [0.02, 2.0]; N_aux 120; core entries x0.3; seeds 0-7), whose core QP equations have their root inside the
-    128-point window [-11, -10] Ha; 100 imaginary points; Pade order M = N_core + N_val + N_Im as in the paper.
-    Also the generic set at the same point counts.  Larger systems of the acene-like recipe carry correlation
+    128-point window [-11, -10] Ha; 100 imaginary points; Pade order M = N_core + N_val + N_Im as in the paper;
+    neighbourhood radii from --delta-c / --delta-v.  Also the generic set at the same point counts.  Larger systems of the acene-like recipe carry correlation
     self-energies of tens of Ha, whose QP roots leave the window."""
     import torch
 

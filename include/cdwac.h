@@ -113,7 +113,7 @@ typedef struct {
   int real_set;        /* cdwac_real_set (GENERIC) */
   int n_core, n_val;   /* REFINED region sizes, n_core + n_val must equal n_real (20, 20: the paper's
                           CD-WAC(20, 20, N_Im) of Sec. 5.1); ignored by GENERIC */
-  double delta_c;      /* REFINED core and valence neighbourhood radii (0.5 Ha, 1.0 Ha; Sec. 3.3 leaves them to */
+  double delta_c;      /* REFINED core and valence neighbourhood radii (0.5 Ha, 0.5 Ha; Sec. 3.3 leaves them to */
   double delta_v;      /*   tuning) */
 } cdwac_params;
 

@@ -562,7 +562,7 @@ class Params:
     n_core: int = 20               # refined set sizes; CD-WAC(20, 20, N_Im) is the paper's recommendation (Sec. 5.1)
     n_val: int = 20
     delta_c: float = 0.5           # neighbourhood radii (Ha), "parameters that can be tuned" (Sec. 3.3)
-    delta_v: float = 1.0
+    delta_v: float = 0.5
 
 
 def run_cdwac(B, D, On, eps, n_occ, states, params: Params, omega_grid, shifts=None, with_sigma=True):

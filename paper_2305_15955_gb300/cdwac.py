@@ -150,10 +150,10 @@ class Params:
     n_core: int = 20
     n_val: int = 20
     delta_c: float = 0.5
-    delta_v: float = 1.0
+    delta_v: float = 0.5
 
     @classmethod
-    def refined(cls, n_core=20, n_val=20, delta_c=0.5, delta_v=1.0, **kw):
+    def refined(cls, n_core=20, n_val=20, delta_c=0.5, delta_v=0.5, **kw):
         """CD-WAC(n_core, n_val, n_imag): the refined near-real set omega_C U omega_V (Sec. 3.3)."""
         return cls(n_real=n_core + n_val, real_set=REAL_REFINED, n_core=n_core, n_val=n_val, delta_c=delta_c,
                    delta_v=delta_v, **kw)

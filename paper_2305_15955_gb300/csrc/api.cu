@@ -193,7 +193,7 @@ void cdwac_default_params(cdwac_params* p) {
   p->n_core = 20;
   p->n_val = 20;
   p->delta_c = 0.5;
-  p->delta_v = 1.0;
+  p->delta_v = 0.5;
 }
 
 cdwac_status cdwac_sync_status(cdwac_ctx* ctx, void* stream) {

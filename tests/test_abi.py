@@ -34,7 +34,7 @@ def test_default_params_and_errors_without_gpu():
     assert (p.real_set, p.n_core, p.n_val, p.delta_c, p.delta_v) == (d.real_set, d.n_core, d.n_val, d.delta_c,
                                                                       d.delta_v)
     # the library filled the binding's struct up to its last field (zero-initialised before the call)
-    assert p.delta_v == 1.0
+    assert p.delta_v == 0.5
     # null arguments are rejected on the host, before any CUDA call
     assert lib.cdwac_create(None, 0) == cdwac.ERR_ARG
     assert lib.cdwac_build_W_imag(None, None, None, None, None, None, None) == cdwac.ERR_ARG

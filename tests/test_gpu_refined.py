@@ -48,7 +48,7 @@ def test_refined_points_match_oracle(ctx, n_core, n_val, delta_c, delta_v):
 def test_refined_cdwac_sigma_and_qp_small(ctx):
     # CD-WAC(20, 20, 100), the paper's recommended split of 40 near-real points
     spec = inputs.small_system()
-    p = cdwac.Params.refined(20, 20, n_imag=100, pade_M=64)
+    p = cdwac.Params.refined(20, 20, delta_c=0.5, delta_v=1.0, n_imag=100, pade_M=64)
     omega = inputs.omega_grid(128)
     r = _wac_case(ctx, spec, p, omega)
     sig_rep, q, sens = r["rep"][0]
@@ -63,7 +63,7 @@ def test_refined_two_states_ragged(ctx):
     spec = inputs.custom_system(70, 9, 200, seed=8, n_core=2, states=(0, 1), core_scale=0.3)
     # CD-WAC(12, 12, 40) with M = 40: a setting whose continuation is well conditioned on much of the grid (with
     # M = 48 nearly every omega is ill conditioned, which leaves only the loose sensitivity-scaled bound)
-    p = cdwac.Params.refined(12, 12, n_imag=40, pade_M=40)
+    p = cdwac.Params.refined(12, 12, delta_c=0.5, delta_v=1.0, n_imag=40, pade_M=40)
     omega = inputs.omega_grid(48)
     r = _wac_case(ctx, spec, p, omega)
     for s in range(2):
