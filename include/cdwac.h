@@ -213,11 +213,12 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
                             const double* omega, int n_grid, double tol, int max_iter, double* e_qp, double* Z,
                             int* iters, int* qp_status, void* stream);
 
-/* Eigenvalue self-consistency beyond G0W0 (Sec. 5.4) for the requested states, CD-WAC.
+/* Eigenvalue self-consistency beyond G0W0 (Sec. 5.4) for the requested states, by CD-WAC (plain_cd 0) or by plain
+ * CD (plain_cd 1: every residue builds W from the cycle's transition energies; the reference CD-WAC is judged by).
  * Cycle k solves the QP equation e_n = eps_n + shift_n + Re Sigma^c_n(e_n) (eps_n: sys->eps) of every requested
  * state with G built from eps_G: sys->eps with the requested entries replaced by the QP energies of cycle k-1
  * (cycle 1 is G0W0); every other orbital keeps its energy.
- *   mode CDWAC_EVGW0  W (imaginary grid and near-real references) and the Thiele fits from sys->eps, built once.
+ *   mode CDWAC_EVGW0  W (imaginary grid, near-real references, residues) and the Thiele fits from sys->eps, built once.
  *        CDWAC_EVGW   W, the near-real references (placed from eps_G) and the fits rebuilt every cycle from eps_G.
  * The I term carries W_nm(0) in closed form (its Lorentzian integrates to sgn(omega - eps_m) pi / 2 whatever the
  * grid), since at self-consistency Sigma_n is evaluated at its own G energy, closer to it than the grid resolves.
@@ -231,7 +232,7 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
  * equation has no solution or max_cycles pass without self-consistency (outputs hold the last cycle), CDWAC_ERR_ARG
  * when an updated level crosses the Fermi level.  Allocates its tables (eps_G, W, W(0), fits) for the call. */
 typedef enum { CDWAC_EVGW0 = 0, CDWAC_EVGW = 1 } cdwac_ev_mode;
-cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode,
+cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode, int plain_cd,
                         const double* shift, const double* omega, int n_grid, double cycle_tol, int max_cycles,
                         double* e_qp, double* Z, int* qp_status, int* cycles, void* stream);
 

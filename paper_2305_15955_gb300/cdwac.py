@@ -115,8 +115,8 @@ def load():
     lib.cdwac_build_W_imag_noalloc.argtypes = [sysp, prmp, P, P, P, P, P]
     lib.cdwac_ldlt_factor.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
     lib.cdwac_spectral.argtypes = [P, sysp, prmp, P, P, P, padep, P, P, ctypes.c_int, P, P, P]
-    lib.cdwac_evgw.argtypes = [P, sysp, prmp, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, P, P,
-                               P, ctypes.POINTER(ctypes.c_int), P]
+    lib.cdwac_evgw.argtypes = [P, sysp, prmp, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_double,
+                               ctypes.c_int, P, P, P, ctypes.POINTER(ctypes.c_int), P]
     lib.cdwac_mlp_features.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P,
                                        ctypes.c_int, P, P, P, P, P]
     lib.cdwac_mlp_loss_grad.argtypes = [P, P, ctypes.c_int, P, P, ctypes.c_int, P, P, P, P, P]
@@ -339,9 +339,11 @@ class Context:
     def _dev(self):
         return torch.device("cuda", self.device)
 
-    def evgw(self, system: System, params: Params, mode, omega_grid, shift=None, cycle_tol=1e-6, max_cycles=30):
+    def evgw(self, system: System, params: Params, mode, omega_grid, shift=None, cycle_tol=1e-6, max_cycles=30,
+             plain_cd=False):
         """cdwac_evgw: (e_qp, Z, qp_status [n_states] on the device, cycles, status).  status is OK or
-        ERR_QP_NOT_CONVERGED (no solution in a cycle, or max_cycles without self-consistency); other errors raise."""
+        ERR_QP_NOT_CONVERGED (no solution in a cycle, or max_cycles without self-consistency); other errors raise.
+        plain_cd: residues from W built at every residue instead of the continued fractions."""
         dev = self._dev()
         grid = torch.as_tensor(omega_grid, dtype=torch.float64).to(dev).contiguous()
         sh = None if shift is None else torch.as_tensor(shift, dtype=torch.float64).to(dev).contiguous()
@@ -351,9 +353,9 @@ class Context:
         qs = torch.empty(ns, dtype=torch.int32, device=dev)
         cycles = ctypes.c_int(0)
         p = params.c()
-        st = self.lib.cdwac_evgw(self.h, ctypes.byref(system.c), ctypes.byref(p), int(mode), _ptr(sh), _ptr(grid),
-                                 int(grid.numel()), float(cycle_tol), int(max_cycles), _ptr(e), _ptr(Z), _ptr(qs),
-                                 ctypes.byref(cycles), self._stream())
+        st = self.lib.cdwac_evgw(self.h, ctypes.byref(system.c), ctypes.byref(p), int(mode), int(bool(plain_cd)),
+                                 _ptr(sh), _ptr(grid), int(grid.numel()), float(cycle_tol), int(max_cycles), _ptr(e),
+                                 _ptr(Z), _ptr(qs), ctypes.byref(cycles), self._stream())
         if st not in (OK, ERR_QP_NOT_CONVERGED):
             self._check(st)
         self.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))

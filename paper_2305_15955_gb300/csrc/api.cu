@@ -703,18 +703,23 @@ cdwac_status cdwac_sigma(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_pa
 }
 
 // Plain-CD quasiparticle solve for one state: host-driven fixed point, one Sigma evaluation per iteration.
+// One state's QP equation with plain CD; eps (host) are the energies of G, en the eps_n of the equation.
+// Optional (evGW): sub_W, whose device energies give W's transition energies (default: sub's); W_zero_s, the
+// state's W_nm(0) row for the closed-form part of the I term; e_start, the first iterate (default: en).
 static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, const cdwac_params* prm,
                                       const double* xi, const double* wxi, const double* W_imag_s,
                                       const std::vector<double>& eps, double en, double sh,
                                       const std::vector<double>& grid, double tol, int max_iter, double* out_e,
-                                      double* out_z, int* out_it, int* out_st, double* dsig, cudaStream_t st) {
+                                      double* out_z, int* out_it, int* out_st, double* dsig, cudaStream_t st,
+                                      const cdwac_system* sub_W = nullptr, const double* W_zero_s = nullptr,
+                                      const double* e_start = nullptr) {
   auto resig = [&](double w, double* val) -> cdwac_status {
     cdwac_status r;
     std::vector<double> wv(1, w);
     // omega must be on the device for the I term: reuse dsig[2..] as the frequency slot
     CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(dsig + 2, &w, sizeof(double), cudaMemcpyHostToDevice, st));
-    if ((r = launch_sigma_wac(ctx, sub, prm, xi, wxi, W_imag_s, nullptr, dsig + 2, 1, dsig, st))) return r;
-    if ((r = plain_cd_residues(ctx, sub, prm, eps, wv, dsig, 1, 0, st))) return r;
+    if ((r = launch_sigma_wac(ctx, sub, prm, xi, wxi, W_imag_s, nullptr, dsig + 2, 1, dsig, st, W_zero_s))) return r;
+    if ((r = plain_cd_residues(ctx, sub_W ? sub_W : sub, prm, eps, wv, dsig, 1, 0, st))) return r;
     double h[2];
     CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(h, dsig, sizeof(h), cudaMemcpyDeviceToHost, st));
     CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
@@ -731,7 +736,7 @@ static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, c
     return CDWAC_OK;
   };
   cdwac_status rc;
-  double e = en, e_new = en, s;
+  double e = e_start ? *e_start : en, e_new = e, s;
   for (int it = 1; it <= max_iter; ++it) {
     if ((rc = resig(e, &s))) return rc;
     e_new = en + sh + s;
@@ -850,7 +855,7 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
 
 namespace {
 struct EvBufs {
-  double *epsG, *xi, *wxi, *W, *W0, *zero;
+  double *epsG, *xi, *wxi, *W, *W0, *zero, *dsig;
   cplx *pa, *pz2;
   int *nodes, *used, *iters;
 };
@@ -862,6 +867,7 @@ void carve_ev(Arena& a, EvBufs& b, int nb, int ns, int ni, int n_occ, int M) {
   b.W = a.take<double>((size_t)ns * ni * nb);
   b.W0 = a.take<double>((size_t)ns * nb);
   b.zero = a.take<double>(1);
+  b.dsig = a.take<double>(4);
   b.pa = a.take<cplx>((size_t)ns * n_occ * M);
   b.pz2 = a.take<cplx>((size_t)ns * n_occ * M);
   b.nodes = a.take<int>((size_t)ns * n_occ * M);
@@ -883,13 +889,13 @@ struct StreamFree {
 }  // namespace
 
 extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode,
-                                   const double* shift, const double* omega, int n_grid, double cycle_tol,
-                                   int max_cycles, double* e_qp, double* Z, int* qp_status, int* cycles,
-                                   void* stream) {
+                                   int plain_cd, const double* shift, const double* omega, int n_grid,
+                                   double cycle_tol, int max_cycles, double* e_qp, double* Z, int* qp_status,
+                                   int* cycles, void* stream) {
   cdwac_status rc = check_system(ctx, sys, prm);
   if (rc) return rc;
-  if ((mode != CDWAC_EVGW0 && mode != CDWAC_EVGW) || !omega || n_grid < 2 || !e_qp || !Z || !qp_status ||
-      !cycles || !(cycle_tol > 0) || max_cycles < 1)
+  if ((mode != CDWAC_EVGW0 && mode != CDWAC_EVGW) || (plain_cd != 0 && plain_cd != 1) || !omega || n_grid < 2 ||
+      !e_qp || !Z || !qp_status || !cycles || !(cycle_tol > 0) || max_cycles < 1)
     return set_error(ctx, CDWAC_ERR_ARG, "bad evgw args");
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
@@ -907,13 +913,16 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
   StreamFree guard{buf, st};
   Arena ar(buf);
   carve_ev(ar, b, nb, ns, ni, n_occ, M);
-  std::vector<double> hG(nb), he(ns);
-  std::vector<int> hs(ns), hst(ns);
+  std::vector<double> hG(nb), hK(nb), he(ns), hz(ns), hsh(ns, 0.0), hgrid(n_grid);
+  std::vector<int> hs(ns), hst(ns), hit(ns);
   CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(b.epsG, sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToDevice, st));
   CDWAC_CUDA_TRY(ctx, cudaMemsetAsync(b.zero, 0, sizeof(double), st));
-  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hG.data(), sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hK.data(), sys->eps, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
   CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hs.data(), sys->states, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+  CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hgrid.data(), omega, sizeof(double) * n_grid, cudaMemcpyDeviceToHost, st));
+  if (shift) CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hsh.data(), shift, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
   CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  hG = hK;
   for (int s = 0; s < ns; ++s)
     if (hs[s] < 0 || hs[s] >= nb) return set_error(ctx, CDWAC_ERR_ARG, "state index %d out of range", hs[s]);
   cdwac_system sysG = *sys;   // G from eps_G
@@ -921,24 +930,47 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
   cdwac_pade pade{ns, n_occ, M, reinterpret_cast<double*>(b.pa), reinterpret_cast<double*>(b.pz2), b.nodes, b.used};
   cdwac_params p0 = *prm;     // W(0): one frequency at xi = 0
   p0.n_imag = 1;
+  // evGW0 keeps W (and for CD-WAC the near-real references and fits) of the KS energies; evGW rebuilds them
+  // from eps_G every cycle
+  const cdwac_system* sw = mode == CDWAC_EVGW ? &sysG : sys;
   int cyc = 1, outcome = 0;   // 1 self-consistent, 2 a QP equation without solution
   for (; cyc <= max_cycles; ++cyc) {
     if (cyc == 1 || mode == CDWAC_EVGW) {
-      // evGW0 keeps W, the near-real references and the fits of the KS energies; evGW rebuilds them from eps_G
-      const cdwac_system* sw = mode == CDWAC_EVGW ? &sysG : sys;
       if ((rc = cdwac_build_W_imag(ctx, sw, prm, b.xi, b.wxi, b.W, st))) return rc;
       if ((rc = build_W_freqs(ctx, sw, &p0, b.zero, b.W0, st))) return rc;
-      if ((rc = cdwac_fit_pade(ctx, sw, prm, b.xi, b.W, nullptr, nullptr, &pade, st))) return rc;
+      if (!plain_cd && (rc = cdwac_fit_pade(ctx, sw, prm, b.xi, b.W, nullptr, nullptr, &pade, st))) return rc;
     }
-    {
-      ProfScope ps(ctx, PROF_QP, st);
-      if ((rc = launch_qp_wac(ctx, &sysG, prm, b.xi, b.wxi, b.W, &pade, shift, omega, n_grid, 1e-7, 100, e_qp, Z,
-                              b.iters, qp_status, st, b.W0, sys->eps)))
-        return rc;
+    if (!plain_cd) {
+      {
+        ProfScope ps(ctx, PROF_QP, st);
+        if ((rc = launch_qp_wac(ctx, &sysG, prm, b.xi, b.wxi, b.W, &pade, shift, omega, n_grid, 1e-7, 100, e_qp,
+                                Z, b.iters, qp_status, st, b.W0, sys->eps)))
+          return rc;
+      }
+      CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(he.data(), e_qp, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
+      CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hst.data(), qp_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
+      CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    } else {
+      // plain CD, one state at a time: I term on G's energies, residues with W of sw's transition energies
+      for (int s = 0; s < ns; ++s) {
+        cdwac_system subG = sysG;
+        subG.n_states = 1;
+        subG.states = sys->states + s;
+        subG.O_n = sys->O_dtype == CDWAC_F64 ? (const void*)((const double*)sys->O_n + (long)s * sys->n_aux * nb)
+                                             : (const void*)((const float*)sys->O_n + (long)s * sys->n_aux * nb);
+        cdwac_system subW = subG;
+        subW.eps = sw->eps;
+        const double start = hG[hs[s]];
+        if ((rc = qp_plain_cd_state(ctx, &subG, prm, b.xi, b.wxi, b.W + (long)s * ni * nb, hG, hK[hs[s]], hsh[s],
+                                    hgrid, 1e-7, 100, &he[s], &hz[s], &hit[s], &hst[s], b.dsig, st, &subW,
+                                    b.W0 + (long)s * nb, &start)))
+          return rc;
+      }
+      CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(e_qp, he.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st));
+      CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(Z, hz.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st));
+      CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(qp_status, hst.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, st));
+      CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     }
-    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(he.data(), e_qp, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
-    CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(hst.data(), qp_status, sizeof(int) * ns, cudaMemcpyDeviceToHost, st));
-    CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     double dmax = 0.0;
     for (int s = 0; s < ns; ++s) {
       if (hst[s] == 2) outcome = 2;

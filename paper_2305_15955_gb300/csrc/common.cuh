@@ -270,7 +270,8 @@ cdwac_status launch_spectral(cdwac_ctx* ctx, const double* eps, const int* state
                              const double* omega, int n_omega, const double* sigma, double* A, cudaStream_t st);
 cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                               const double* wxi, const double* W_imag, const cdwac_pade* pade,
-                              const double* omega, int n_omega, double* sigma, cudaStream_t st);
+                              const double* omega, int n_omega, double* sigma, cudaStream_t st,
+                              const double* W_zero = nullptr);
 cdwac_status launch_sigma_I_only(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm,
                                  const double* xi, const double* wxi, const double* W_imag, const double* omega,
                                  int n_omega, double* sigma, cudaStream_t st);

@@ -310,9 +310,10 @@ cdwac_status launch_spectral(cdwac_ctx* ctx, const double* eps, const int* state
 
 cdwac_status launch_sigma_wac(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, const double* xi,
                               const double* wxi, const double* W_imag, const cdwac_pade* pade, const double* omega,
-                              int n_omega, double* sigma, cudaStream_t st) {
+                              int n_omega, double* sigma, cudaStream_t st, const double* W_zero) {
   if (n_omega <= 0) return CDWAC_OK;
   SigmaArgs A = make_args(sys, prm, xi, wxi, W_imag, pade);
+  A.W_zero = W_zero;
   dim3 grid(n_omega, sys->n_states);
   sigma_kernel<<<grid, SIG_THREADS, 0, st>>>(A, omega, n_omega, reinterpret_cast<cplx*>(sigma), ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);

@@ -39,5 +39,5 @@ def test_default_params_and_errors_without_gpu():
     assert lib.cdwac_create(None, 0) == cdwac.ERR_ARG
     assert lib.cdwac_build_W_imag(None, None, None, None, None, None, None) == cdwac.ERR_ARG
     cyc = ctypes.c_int(0)
-    assert lib.cdwac_evgw(None, None, None, 0, None, None, 0, 1e-6, 1, None, None, None, ctypes.byref(cyc),
+    assert lib.cdwac_evgw(None, None, None, 0, 0, None, None, 0, 1e-6, 1, None, None, None, ctypes.byref(cyc),
                           None) == cdwac.ERR_ARG
