@@ -511,7 +511,8 @@ def run_refined_map(args, rank, ws, dist):
     small recipe (N_basis 40: one core level at -10.6 Ha, 4 valence levels in [-1.1, -0.3], 35 virtuals log-spaced
     in [0.02, 2.0]; N_aux 120; core entries x0.3; seeds 0-7), whose core QP equations have their root inside the
     128-point window [-11, -10] Ha; 100 imaginary points; Pade order M = N_core + N_val + N_Im as in the paper;
-    neighbourhood radii from --delta-c / --delta-v.  Also the generic set at the same point counts.  Larger systems of the acene-like recipe carry correlation
+    neighbourhood radii from --delta-c / --delta-v.  Also the generic set at the same point counts, and evGW0 / evGW
+    cycles of CD-WAC against plain-CD cycles.  Larger systems of the acene-like recipe carry correlation
     self-energies of tens of Ha, whose QP roots leave the window."""
     import torch
 
@@ -563,6 +564,22 @@ def run_refined_map(args, rank, ws, dist):
     for nr in (10, 20, 40, 80):
         m, x, b = stats(errors(cdwac.Params(n_imag=ni, n_real=nr, pade_M=min(cdwac.MAX_M, ni + nr))))
         generic[str(nr)] = {"mae_meV": m, "max_meV": x, "not_converged": b}
+    # evGW0 / evGW (Sec. 5.4): CD-WAC cycles against plain-CD cycles on the same systems
+    evgw = {}
+    for mode_name, mode in (("evGW0", cdwac.EVGW0), ("evGW", cdwac.EVGW)):
+        ref = []
+        for sysd, *_ in systems:
+            e, _, _, _, st = ctx.evgw(sysd, base, mode, omega, plain_cd=True)
+            ref.append(float(e.cpu()[0]) if st == cdwac.OK else None)
+        for name, p in (("generic 20", cdwac.Params(n_imag=ni, n_real=20, pade_M=min(cdwac.MAX_M, ni + 20))),
+                        ("refined (10, 10), delta_v 0.25", cdwac.Params.refined(10, 10, 0.5, 0.25, n_imag=ni,
+                                                                                pade_M=min(cdwac.MAX_M, ni + 20)))):
+            errs = []
+            for (sysd, *_), r in zip(systems, ref):
+                e, _, _, _, st = ctx.evgw(sysd, p, mode, omega)
+                errs.append(abs(float(e.cpu()[0]) - r) / HA_PER_MEV if st == cdwac.OK and r is not None else None)
+            m, x, b = stats(errs)
+            evgw[f"{mode_name}, {name}"] = {"mae_meV": m, "max_meV": x, "not_converged": b}
     line = {"metric": "core QP error of CD-WAC(N_core, N_val, N_Im) against plain CD (MAE over 8 systems)",
             "unit": "meV", "dtype": "f64", "data": "synthetic",
             "config": {"workload": "8 small systems: N_basis=40 (1 core at -10.6 Ha, 4 valence in [-1.1,-0.3], 35 "
@@ -570,7 +587,7 @@ def run_refined_map(args, rank, ws, dist):
                                    "core state n=0; 128 omega in [-11,-10] Ha", "n_imag": ni,
                        "delta_c_Ha": args.delta_c, "delta_v_Ha": args.delta_v, "pade_M": "N_core + N_val + N_Im"},
             "sizes": list(sizes), "rows": "N_core", "cols": "N_val", "mae_meV": mae, "max_meV": mx,
-            "not_converged": bad, "generic": generic, "plain_cd_qp_s": t_cd,
+            "not_converged": bad, "generic": generic, "evgw_vs_plain_cd": evgw, "plain_cd_qp_s": t_cd,
             "plain_cd_qp_status": [s[5] for s in systems]}
     print(json.dumps(line), flush=True)
     ctx.close()
