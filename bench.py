@@ -51,6 +51,10 @@ def parse():
                          "of refined-set sizes (one JSON line)")
     ap.add_argument("--delta-c", type=float, default=0.5, help="refined core neighbourhood radius (Ha) of the map")
     ap.add_argument("--delta-v", type=float, default=0.5, help="refined valence neighbourhood radius (Ha) of the map")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="instead of the timed steps: one step of --workload at --precision, its W tables, greedy node "
+                         "orders and Sigma compared with the stored FP64 oracle result (one JSON line)")
+    ap.add_argument("--dump", default=None, help="with --accuracy: write the GPU tables to this .npz file")
     return ap.parse_args()
 
 
@@ -572,8 +576,8 @@ def run_refined_map(args, rank, ws, dist):
             e, _, _, _, st = ctx.evgw(sysd, base, mode, omega, plain_cd=True)
             ref.append(float(e.cpu()[0]) if st == cdwac.OK else None)
         for name, p in (("generic 20", cdwac.Params(n_imag=ni, n_real=20, pade_M=min(cdwac.MAX_M, ni + 20))),
-                        ("refined (10, 10), delta_v 0.25", cdwac.Params.refined(10, 10, 0.5, 0.25, n_imag=ni,
-                                                                                pade_M=min(cdwac.MAX_M, ni + 20)))):
+                        ("refined (10, 10), delta_c 0.5, delta_v 0.25 (fixed radii, not --delta-c/--delta-v)",
+                         cdwac.Params.refined(10, 10, 0.5, 0.25, n_imag=ni, pade_M=min(cdwac.MAX_M, ni + 20)))):
             errs = []
             for (sysd, *_), r in zip(systems, ref):
                 e, _, _, _, st = ctx.evgw(sysd, p, mode, omega)
@@ -593,6 +597,103 @@ def run_refined_map(args, rank, ws, dist):
     ctx.close()
 
 
+def run_accuracy(args, rank, ws, dist):
+    """One untimed step of the workload in the chosen precision and its accuracy against the stored oracle result
+    (tests/golden/acene_1200_cdwac_oracle.json and, when present, the full tables in the matching .npz written by
+    tests/golden/make_acene_reference.py): W(i xi) and W(z) at every stored entry, Sigma over the 128-point window
+    as computed on the GPU and as the oracle's continuation gives it from the GPU's own W tables along the GPU's
+    node orders (which separates the W arithmetic from the continuation's arithmetic), the QP energy."""
+    import torch
+
+    import __graft_entry__ as g
+    from paper_2305_15955_gb300 import cdwac, inputs
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    g.build()
+    spec, desc = workload(args.workload)
+    mixed = args.precision == "mixed"
+    eps = inputs.eigenvalues(spec)
+    B = inputs.build_B(spec, dtype=np.float32 if mixed else np.float64)
+    On = inputs.build_On(spec, dtype=np.float32 if mixed else np.float64)
+    omega = inputs.omega_grid(128)
+    sysd = cdwac.System(eps, B, On, spec.states, spec.n_occ, device=dev)
+    prm = cdwac.Params(n_imag=args.n_imag, n_real=args.n_real, pade_M=min(64, args.n_imag + args.n_real),
+                       precision=cdwac.PREC_MIXED if mixed else cdwac.PREC_FP64)
+    ctx = cdwac.Context(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xi, wxi, W = ctx.build_W_imag(sysd, prm)
+    pade = ctx.fit_pade(sysd, prm, xi, W)
+    sig = ctx.sigma(sysd, prm, xi, wxi, W, pade, torch.as_tensor(omega, device=dev))
+    e, Z, it, qs = ctx.qp_solve(sysd, prm, xi, wxi, W, pade, torch.as_tensor(omega, device=dev))
+    torch.cuda.synchronize()
+    t_step = time.perf_counter() - t0
+    tab = {"xi": xi.cpu().numpy(), "wxi": wxi.cpu().numpy(), "W_imag": W.cpu().numpy()[0],
+           "z_real": pade.z_real.cpu().numpy()[0], "W_real": pade.W_real.cpu().numpy()[0],
+           "nodes": pade.nodes.cpu().numpy()[0], "n_used": pade.n_used.cpu().numpy()[0],
+           "sigma": sig.cpu().numpy()[0], "e_qp": float(e.cpu()[0]), "qp_status": int(qs.cpu()[0])}
+    ctx.close()
+    if args.dump:
+        np.savez(args.dump, **{k: np.asarray(v) for k, v in tab.items()})
+    line = {"mode": "accuracy", "workload": desc, "precision": args.precision, "step_s_untimed": t_step,
+            "qp": {"e_qp_Ha": tab["e_qp"], "status": tab["qp_status"]}}
+    gold = os.path.join(ROOT, "tests", "golden", "acene_1200_cdwac_oracle.json")
+    if args.workload == "acene" and os.path.exists(gold):
+        with open(gold) as f:
+            ref = json.load(f)
+        Wn, Wr = tab["W_imag"], tab["W_real"]
+        rel_i = [abs(Wn[k, m] - v) / abs(v) for k, m, v in ref["W_imag_samples"]]
+        rel_r = [abs(Wr[j, m] - complex(vr, vi)) / abs(complex(vr, vi)) for j, m, vr, vi in ref["W_real_samples"]]
+        sig_ref = np.asarray(ref["sigma_re"]) + 1j * np.asarray(ref["sigma_im"])
+        line["vs_stored_oracle"] = {
+            "W_imag_samples_max_rel_err": float(max(rel_i)), "W_real_samples_max_rel_err": float(max(rel_r)),
+            "W_real_samples_rel_err_by_point": {str(j): float(max(abs(Wr[jj, m] - complex(vr, vi)) / abs(complex(vr, vi))
+                                                                  for jj, m, vr, vi in ref["W_real_samples"] if jj == j))
+                                                for j in sorted({int(x[0]) for x in ref["W_real_samples"]})},
+            "sigma_max_abs_err_meV": float(np.max(np.abs(tab["sigma"] - sig_ref))) / HA_PER_MEV,
+            "sigma_max_abs_meV": float(np.max(np.abs(sig_ref))) / HA_PER_MEV,
+            "qp_oracle_Ha": ref["qp"]["e_qp"]}
+        full = gold.replace(".json", ".npz")
+        if os.path.exists(full):
+            line["vs_stored_oracle"].update(_full_table_comparison(full, tab, eps, spec.n_occ, omega))
+    print(json.dumps(line), flush=True)
+
+
+def _full_table_comparison(path, tab, eps, n_occ, omega):
+    """Every stored oracle table entry against the GPU's, and Sigma from the oracle's continuation arithmetic: on the
+    oracle's W along the oracle's node orders (the stored Sigma), on the GPU's W along the oracle's orders, and on
+    the GPU's W along the GPU's orders."""
+    from oracle import cdwac_oracle as o
+    ref = np.load(path)
+    out = {}
+    rel = lambda a, b: np.abs(a - b) / np.maximum(np.abs(b).max(axis=-1, keepdims=True), 1e-300)
+    out["W_imag_max_rel_err_by_k"] = rel(tab["W_imag"], ref["W_imag"]).max(axis=1).tolist()
+    out["W_real_max_rel_err_by_point"] = rel(tab["W_real"], ref["W_real"]).max(axis=1).tolist()
+    xi, wxi, zr = ref["xi"], ref["wxi"], ref["z_real"]
+    zc = np.concatenate([1j * xi, zr])
+
+    def sigma_from(Wim, Wre, orders, used):
+        fits = [o.thiele_replay(zc, np.concatenate([Wim[:, m].astype(complex), Wre[:, m]]),
+                                orders[m, :used[m]])[0] for m in range(n_occ)]
+        model = o.WacModel(fits=fits)
+        return np.array([o.sigma_c_wac(model, Wim, eps, n_occ, xi, wxi, w, 1e-3) for w in omega])
+
+    s_ref = ref["sigma"]
+    s_gw_oo = sigma_from(tab["W_imag"], tab["W_real"], ref["nodes"], ref["n_used"])
+    s_gw_go = sigma_from(tab["W_imag"], tab["W_real"], tab["nodes"], tab["n_used"])
+    mev = lambda x: float(np.max(np.abs(x))) / HA_PER_MEV
+    out["sigma_gpuW_oracle_orders_vs_oracle_meV"] = mev(s_gw_oo - s_ref)
+    out["sigma_gpuW_gpu_orders_vs_oracle_meV"] = mev(s_gw_go - s_ref)
+    out["sigma_gpu_vs_oracle_arith_same_W_and_orders_meV"] = mev(tab["sigma"] - s_gw_go)
+    out["node_orders_identical_fraction"] = float(np.mean([np.array_equal(tab["nodes"][m, :tab["n_used"][m]],
+                                                                          ref["nodes"][m, :ref["n_used"][m]])
+                                                           for m in range(n_occ)]))
+    return out
+
+
 def main():
     args = parse()
     rank, ws, dist = dist_init()
@@ -600,6 +701,8 @@ def main():
         run_reference(args, rank, ws, dist)
     elif args.refined_map:
         run_refined_map(args, rank, ws, dist)
+    elif args.accuracy:
+        run_accuracy(args, rank, ws, dist)
     elif args.workload == "batch":
         run_batch(args, rank, ws, dist)
     else:

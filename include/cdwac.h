@@ -228,9 +228,12 @@ cdwac_status cdwac_qp_solve(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac
  *   max_cycles              at least 1
  *   e_qp, Z, qp_status [n_states] out (device): the last cycle's QP solutions (qp_status as cdwac_qp_solve)
  *   cycles      [1]         out (HOST int): cycles run
- * Host-driven: the call synchronises `stream` once per cycle.  Returns CDWAC_ERR_QP_NOT_CONVERGED when a QP
- * equation has no solution or max_cycles pass without self-consistency (outputs hold the last cycle), CDWAC_ERR_ARG
- * when an updated level crosses the Fermi level.  Allocates its tables (eps_G, W, W(0), fits) for the call. */
+ * Every cycle's QP fixed point starts from eps_n (the KS level, as in G0W0) and stops at |e_k+1 - e_k| <
+ * min(1e-7, cycle_tol / 10) Ha, at most 100 iterations.
+ * Host-driven: the call synchronises `stream` once per cycle.  Returns CDWAC_ERR_QP_NOT_CONVERGED (cdwac_last_error
+ * says which) when a QP equation has no solution, when an updated level crosses the Fermi level (the transition
+ * energies of W must stay positive) or when max_cycles pass without self-consistency; *cycles and the outputs then
+ * hold the last cycle run.  Allocates its tables (eps_G, W, W(0), fits) for the call. */
 typedef enum { CDWAC_EVGW0 = 0, CDWAC_EVGW = 1 } cdwac_ev_mode;
 cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_params* prm, int mode, int plain_cd,
                         const double* shift, const double* omega, int n_grid, double cycle_tol, int max_cycles,

@@ -705,14 +705,13 @@ cdwac_status cdwac_sigma(cdwac_ctx* ctx, const cdwac_system* sys, const cdwac_pa
 // Plain-CD quasiparticle solve for one state: host-driven fixed point, one Sigma evaluation per iteration.
 // One state's QP equation with plain CD; eps (host) are the energies of G, en the eps_n of the equation.
 // Optional (evGW): sub_W, whose device energies give W's transition energies (default: sub's); W_zero_s, the
-// state's W_nm(0) row for the closed-form part of the I term; e_start, the first iterate (default: en).
+// state's W_nm(0) row for the closed-form part of the I term.  The fixed point starts from en.
 static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, const cdwac_params* prm,
                                       const double* xi, const double* wxi, const double* W_imag_s,
                                       const std::vector<double>& eps, double en, double sh,
                                       const std::vector<double>& grid, double tol, int max_iter, double* out_e,
                                       double* out_z, int* out_it, int* out_st, double* dsig, cudaStream_t st,
-                                      const cdwac_system* sub_W = nullptr, const double* W_zero_s = nullptr,
-                                      const double* e_start = nullptr) {
+                                      const cdwac_system* sub_W = nullptr, const double* W_zero_s = nullptr) {
   auto resig = [&](double w, double* val) -> cdwac_status {
     cdwac_status r;
     std::vector<double> wv(1, w);
@@ -736,7 +735,7 @@ static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, c
     return CDWAC_OK;
   };
   cdwac_status rc;
-  double e = e_start ? *e_start : en, e_new = e, s;
+  double e = en, e_new = e, s;
   for (int it = 1; it <= max_iter; ++it) {
     if ((rc = resig(e, &s))) return rc;
     e_new = en + sh + s;
@@ -900,6 +899,8 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int ns = sys->n_states, nb = sys->n_basis, n_occ = sys->n_occ, ni = prm->n_imag, M = prm->pade_M;
+  // each cycle's QP equation is solved ten times tighter than the self-consistency it is judged by
+  const double inner_tol = std::min(1e-7, 0.1 * cycle_tol);
   // tables kept across the cycles (the W builds use the context scratch for their own work)
   Arena dry(nullptr);
   EvBufs b;
@@ -933,7 +934,7 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
   // evGW0 keeps W (and for CD-WAC the near-real references and fits) of the KS energies; evGW rebuilds them
   // from eps_G every cycle
   const cdwac_system* sw = mode == CDWAC_EVGW ? &sysG : sys;
-  int cyc = 1, outcome = 0;   // 1 self-consistent, 2 a QP equation without solution
+  int cyc = 1, outcome = 0;   // 1 self-consistent, 2 a QP equation without solution, 3 a level crossed eps_F
   for (; cyc <= max_cycles; ++cyc) {
     if (cyc == 1 || mode == CDWAC_EVGW) {
       if ((rc = cdwac_build_W_imag(ctx, sw, prm, b.xi, b.wxi, b.W, st))) return rc;
@@ -943,8 +944,8 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
     if (!plain_cd) {
       {
         ProfScope ps(ctx, PROF_QP, st);
-        if ((rc = launch_qp_wac(ctx, &sysG, prm, b.xi, b.wxi, b.W, &pade, shift, omega, n_grid, 1e-7, 100, e_qp,
-                                Z, b.iters, qp_status, st, b.W0, sys->eps)))
+        if ((rc = launch_qp_wac(ctx, &sysG, prm, b.xi, b.wxi, b.W, &pade, shift, omega, n_grid, inner_tol, 100,
+                                e_qp, Z, b.iters, qp_status, st, b.W0, sys->eps)))
           return rc;
       }
       CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(he.data(), e_qp, sizeof(double) * ns, cudaMemcpyDeviceToHost, st));
@@ -960,10 +961,9 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
                                              : (const void*)((const float*)sys->O_n + (long)s * sys->n_aux * nb);
         cdwac_system subW = subG;
         subW.eps = sw->eps;
-        const double start = hG[hs[s]];
         if ((rc = qp_plain_cd_state(ctx, &subG, prm, b.xi, b.wxi, b.W + (long)s * ni * nb, hG, hK[hs[s]], hsh[s],
-                                    hgrid, 1e-7, 100, &he[s], &hz[s], &hit[s], &hst[s], b.dsig, st, &subW,
-                                    b.W0 + (long)s * nb, &start)))
+                                    hgrid, inner_tol, 100, &he[s], &hz[s], &hit[s], &hst[s], b.dsig, st, &subW,
+                                    b.W0 + (long)s * nb)))
           return rc;
       }
       CDWAC_CUDA_TRY(ctx, cudaMemcpyAsync(e_qp, he.data(), sizeof(double) * ns, cudaMemcpyHostToDevice, st));
@@ -985,15 +985,19 @@ extern "C" cdwac_status cdwac_evgw(cdwac_ctx* ctx, const cdwac_system* sys, cons
     // every transition energy eps_a - eps_i must stay positive
     const double top_occ = *std::max_element(hG.begin(), hG.begin() + n_occ);
     const double low_virt = *std::min_element(hG.begin() + n_occ, hG.end());
-    if (!(top_occ < low_virt))
-      return set_error(ctx, CDWAC_ERR_ARG, "evgw: an updated level crossed the Fermi level (cycle %d)", cyc);
+    if (!(top_occ < low_virt)) {
+      outcome = 3;
+      break;
+    }
     if ((rc = launch_scatter_states(ctx, b.epsG, sys->states, e_qp, ns, st))) return rc;
   }
   *cycles = cyc > max_cycles ? max_cycles : cyc;
   CDWAC_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if (outcome == 1) return CDWAC_OK;
-  return set_error(ctx, CDWAC_ERR_QP_NOT_CONVERGED, outcome == 2 ? "evgw: a QP equation has no solution (cycle %d)"
-                                                                  : "evgw: not self-consistent after %d cycles",
+  return set_error(ctx, CDWAC_ERR_QP_NOT_CONVERGED,
+                   outcome == 2   ? "evgw: a QP equation has no solution (cycle %d)"
+                   : outcome == 3 ? "evgw: an updated level crossed the Fermi level (cycle %d)"
+                                  : "evgw: not self-consistent after %d cycles",
                    *cycles);
 }
 

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(SIG_THREADS) qp_kernel(SigmaArgs A, const doub
     double d = (resig(e + h) - resig(e - h)) / (2.0 * h);
     return 1.0 / (1.0 - d);
   };
-  double e = A.eps[A.states[s]];     // the fixed point starts from the state's energy in G
+  double e = en;     // the fixed point starts from eps_n of the equation (the KS level, in every evGW cycle too)
   int it = 1;
   int conv = 0;
   double e_new = e;

@@ -127,6 +127,39 @@ def test_cd_matches_sum_over_poles_other_state(small):
         assert abs(cd.real - ps.real) < 1e-10 * max(1.0, abs(ps))
 
 
+def test_sigma_x_hand_example():
+    # Eq. exs for two auxiliary functions and three orbitals, two of them occupied, worked by hand:
+    # Sigma^x_n = -[(0.5)^2 + (-1)^2 + (0.25)^2 + 2^2] = -5.3125; the virtual column (3, -7) does not enter
+    On_s = np.array([[0.5, -1.0, 3.0], [0.25, 2.0, -7.0]])
+    assert o.sigma_x(On_s, 2) == -5.3125
+    assert o.sigma_x(On_s, 1) == -0.3125
+
+
+def test_sigma_R_poles_with_exact_rpa_poles_equals_plain_cd(small):
+    # the pole-residue form of W behind Eq. sigma_pole is exact when it carries every RPA excitation Omega_s with
+    # residue (w^s_nm)^2: the residue term from that model equals plain CD's W built at every residue
+    s = small
+    n_occ = s["spec"].n_occ
+    Om, Z = o.rpa_poles(s["B"], s["D"])
+    wamp = o.pole_amplitudes(s["B"], s["D"], s["On"][0], Om, Z)            # [N_b, n_poles]
+    poles = np.stack([np.broadcast_to(Om, (n_occ, len(Om))), wamp[:n_occ] ** 2], axis=-1)
+    for w in (-10.9, -10.3, -0.95, -0.5):
+        ref = o.sigma_R_cd(s["B"], s["D"], s["On"][0], s["eps"], n_occ, w, 1e-3)
+        got = o.sigma_R_poles(poles, s["eps"], n_occ, w, 1e-3)
+        assert abs(ref) > 1e-3
+        assert abs(got - ref) < 1e-10 * max(1.0, abs(ref)), (w, got, ref)
+    # a single pole per m reproduces the closed-form one-pole W of an N_aux = 1, N_ov = 1 system
+    b, o00, d, e0, e1 = 0.6, 0.7, 9.5, -10.0, -0.5
+    om = math.sqrt(d * d + 4 * b * b * d)
+    r = 2 * o00 ** 2 * b ** 2 * d / om
+    eps2 = np.array([e0, e1, e1 + d])
+    pol = np.array([[[om, 0.0]], [[om, r]]])
+    w = -5.0
+    z = abs(e1 - w) + 1e-3j
+    expect = -(4 * o00 ** 2 * b ** 2 * d / (z * z - d * d - 4 * b * b * d))     # -f_m W(z), f_m = -1
+    assert abs(o.sigma_R_poles(pol, eps2, 2, w, 1e-3) - expect) < 1e-13
+
+
 def test_sigma_x_definition(small):
     s = small
     On = s["On"][0]
