@@ -98,7 +98,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
 
 static const char* kProfNames[PROF_COUNT] = {"grid",      "pi_prep",   "pi_tc_imag", "pi_tc_complex", "pi_fp64_simt",
                                               "ldlt",      "w_solves",  "thiele_fit", "sigma",         "qp_solve",
-                                              "mlp",       "ldlt_diag", "ldlt_panel", "ldlt_update"};
+                                              "mlp",       "ldlt_diag", "ldlt_panel", "ldlt_update", "ldlt_slice"};
 
 void cdwac_profile_enable(cdwac_ctx* ctx, int on) {
   if (ctx) ctx->prof = on < 0 ? 0 : (on > 2 ? 2 : on);

@@ -37,6 +37,7 @@ enum ProfClass {
   PROF_LDLT_DIAG,     // fine level: the three launches of each LDL^T block step
   PROF_LDLT_PANEL,
   PROF_LDLT_UPDATE,
+  PROF_LDLT_SLICE,    // fine level: digit planes of the panel for the tensor-core updates
   PROF_COUNT
 };
 

@@ -37,6 +37,11 @@ __device__ inline cplx shfl_xor_T(cplx v, int m) {
   return mkc(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+__device__ inline double shfl_T(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ inline cplx shfl_T(cplx v, int src) {
+  return mkc(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
 __device__ inline unsigned pivot_err(double) { return DEV_ERR_NOT_SPD; }
 __device__ inline unsigned pivot_err(cplx) { return DEV_ERR_SINGULAR; }
 
@@ -80,12 +85,15 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (tid < NB) {
+    if (tid < NB) {                                   // warps 0 and 1, whole
       const T d0 = S[j * SD + j];
       const bool bad = bad_pivot_fast(d0);
       if (tid == 0) bad_step = bad ? 1 : 0;
+      // one reciprocal per warp, broadcast (FP64 division is a multi-instruction sequence on the scarce FP64 units)
+      T rinv = N::one();
+      if ((tid & 31) == 0) rinv = N::div(N::one(), bad ? N::one() : d0);
+      rinv = shfl_T(rinv, 0);
       if (tid > j && tid < nb) {
-        const T rinv = N::div(N::one(), bad ? N::one() : d0);
         const T u = S[tid * SD + j];
         ucol[tid] = u;
         lcol[tid] = N::mul(u, rinv);
@@ -531,8 +539,11 @@ static cdwac_status ldlt_factor_lookahead(cdwac_ctx* ctx, T* A, int n, T* dinv, 
       ProfScope ps(ctx, PROF_LDLT_PANEL, st, 2);
       panel_kernel<T><<<ceil_div(rest, PR), PT, psmem, st>>>(A, n, k0, dinv, w);
       CDWAC_LAUNCH_CHECK(ctx);
+    }
+    if (oz) {
       // digit planes of this step (double-buffered like the panel: the side stream may still read step kb - 1)
-      if (oz && (rc = ozaki_slice<T>(ctx, *oz, kb & 1, A, n, k0, w, st))) return rc;
+      ProfScope pss(ctx, PROF_LDLT_SLICE, st, 2);
+      if ((rc = ozaki_slice<T>(ctx, *oz, kb & 1, A, n, k0, w, st))) return rc;
     }
     if (bulk_pending) CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(st, ctx->ev_bulk, 0));
     bulk_pending = false;
@@ -618,12 +629,16 @@ cdwac_status ldlt_factor(cdwac_ctx* ctx, T* A, int n, T* dinv, T* linv_blocks, T
       panel_kernel<T><<<ceil_div(rest, PR), PT, psmem, st>>>(A, n, k0, dinv, wpanel);
       CDWAC_LAUNCH_CHECK(ctx);
     }
-    ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
     if (oz) {
       cdwac_status rc;
-      if ((rc = ozaki_slice<T>(ctx, *oz, 0, A, n, k0, wpanel, st))) return rc;
+      {
+        ProfScope pss(ctx, PROF_LDLT_SLICE, st, 2);
+        if ((rc = ozaki_slice<T>(ctx, *oz, 0, A, n, k0, wpanel, st))) return rc;
+      }
+      ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
       if ((rc = ozaki_update<T>(ctx, *oz, 0, A, n, k0, 0, st))) return rc;
     } else {
+      ProfScope ps(ctx, PROF_LDLT_UPDATE, st, 2);
       update_kernel<T><<<rblk * (rblk + 1) / 2, 256, 0, st>>>(A, n, k0, wpanel, 0);
       CDWAC_LAUNCH_CHECK(ctx);
     }

@@ -8,13 +8,14 @@
 // dropped).  On the imaginary axis -w = 4 D / (xi^2 + D^2) > 0 and one real accumulator is used; for complex z
 // the real and imaginary parts of -w give two scaled operands that share the loaded B tile (two accumulators).
 //
-// Kernel: one CTA per 128 x 128 tile of the lower triangle of A (lower-triangle tiles only: A is symmetric),
-// 128 threads.  Warp 0 lane 0 drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory
-// stages; warp 1 owns the tensor memory and lane 0 issues tcgen05.mma (M = 128, N = 128, K = 16 per instruction,
-// both operands K-major); tcgen05.commit releases a stage when the MMAs reading it finish.  All four warps then
-// read the accumulator rows they own (tcgen05.ld 32x32b) and write A in FP64.  Every wait on an mbarrier is
-// bounded (5 s): on expiry the kernel records CDWAC_ERR_TIMEOUT, stops issuing, drains what it issued and frees
-// its tensor memory.
+// Kernel: one CTA per 128 x 128 (real) or 128 x 64 (complex) tile of the lower triangle of A (A is symmetric),
+// 384 threads.  Warp 0 lane 0 drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory
+// stages; warp 1 owns the tensor memory and lane 0 issues tcgen05.mma (M = 128, N = 128 or 64, K = 16 per
+// instruction, both operands K-major); tcgen05.commit releases a stage when the MMAs reading it finish.  The hi*hi
+// products of every K-tile and the corrections of every 8 K-tiles go to fresh accumulators (double-buffered in
+// tensor memory); warps 4-11 read each finished one (tcgen05.ld 32x32b, the accumulator rows they own), add it
+// into FP32 running sums and at the end write A in FP64.  Every wait on an mbarrier is bounded (5 s): on expiry the kernel records
+// CDWAC_ERR_TIMEOUT, stops issuing, drains what it issued and frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -27,7 +28,7 @@
 namespace {
 using namespace tc;
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BK = 64;                     // tile rows and K-tile width (tile columns: Cfg::BN)
 constexpr int PLANE = BM * BK * 2;                       // bytes of one 128 x 64 BF16 operand tile
 struct Maps {
   CUtensorMap a0h, a0l, a1h, a1l, bh, bl;
@@ -72,37 +73,62 @@ __device__ inline void grouped_tile_coords(int b, int nt, int& ti, int& tj) {
   ti = tj = nt;   // past the triangle: not reached for b < nt (nt + 1) / 2
 }
 
+// Accumulation in chunks.  The FP32 accumulation of the tensor cores is not unbiased over a long chain: each
+// instruction that adds into an accumulator loses a fraction of an ulp of it, always towards zero.  Summed over all
+// K = 129 600 columns of the acene-like system (8100 K-steps of three products into one accumulator) Pi came out
+// about 1.2e-3 too small in magnitude, a bias that survives in W at large xi.  So the hi*hi products of every
+// K-tile (64 columns, a chain of four instructions) go to a fresh accumulator, and the hi*lo + lo*hi corrections
+// (2^-8 of the size: their chain bias is negligible) to a second one refreshed every CORR K-tiles; both are
+// double-buffered in tensor memory, and a drain warpgroup adds every finished accumulator into FP32 running sums
+// with round-to-nearest adds on the CUDA cores while the MMAs fill the other buffers.
+constexpr int CORR = 8;
+
 template <int NACC>
 struct Cfg {
-  static constexpr int NPL = 2 * NACC + 2;                 // operand planes per stage
-  static constexpr int STAGE = NPL * PLANE;
+  static constexpr int BN = NACC == 1 ? 128 : 64;          // tile columns: the drain holds NACC x BN = 128 sums
+  static constexpr int B_PLANE = BN * BK * 2;
+  static constexpr int STAGE = 2 * NACC * PLANE + 2 * B_PLANE;
   static constexpr int STAGES = NACC == 1 ? 3 : 2;
   static constexpr int SMEM = STAGES * STAGE + 1024;       // + alignment slack
-  static constexpr int TMEM_COLS = NACC == 1 ? 128 : 256;
+  static constexpr int ACC_COLS = NACC * BN;               // tensor-memory columns of one accumulator set
+  static constexpr int TMEM_COLS = 4 * ACC_COLS;           // hi*hi and corrections, two buffers each: 512
 };
 
-// A = I + S B^T (lower triangle).  NACC == 1: real A (double*).  NACC == 2: complex A (cplx*), re from S0, im from S1.
+// A = I + S B^T (lower triangle).  NACC == 1: real A (double*), 128 x 128 tiles.  NACC == 2: complex A (cplx*),
+// re from S0 and im from S1, 128 x 64 tiles (two per 128 x 128 tile of the triangle).
+// Warps: 0 = TMA producer (lane 0), 1 = tensor-memory owner and MMA issuer (lane 0), 4..11 = two drain warpgroups
+// (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the tile rows it later writes); 2, 3 idle.
 template <int NACC>
-__global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
+__global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
                                                          void* A_out, float* negpi32, unsigned* status) {
   using C = Cfg<NACC>;
+  constexpr int BNC = C::BN;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[C::STAGES];
   __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t hh_full[2], hh_empty[2], cr_full[2], cr_empty[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ int issued, consumed;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nt = (n + BM - 1) / BM;
   int ti, tj;
-  grouped_tile_coords(blockIdx.x, (n + BM - 1) / BM, ti, tj);
-
+  grouped_tile_coords(NACC == 1 ? blockIdx.x : blockIdx.x >> 1, nt, ti, tj);
+  const int row0 = ti * BM, col0 = tj * BM + (NACC == 1 ? 0 : (blockIdx.x & 1) * BNC);
+  if (col0 >= n || col0 > row0 + BM - 1) return;   // nothing of the triangle here: the whole CTA leaves at once
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&hh_full[b], 1);
+      mbar_init(&hh_empty[b], 8);
+      mbar_init(&cr_full[b], 1);
+      mbar_init(&cr_empty[b], 8);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -134,23 +160,35 @@ __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__
       mbar_expect_tx(&full_bar[s], (uint32_t)C::STAGE);
       uint8_t* st = smem + s * C::STAGE;
       const int x = kt * BK;
-      tma_load_2d(&maps.a0h, &full_bar[s], st + 0 * PLANE, x, ti * BM);
-      tma_load_2d(&maps.a0l, &full_bar[s], st + 1 * PLANE, x, ti * BM);
+      tma_load_2d(&maps.a0h, &full_bar[s], st + 0 * PLANE, x, row0);
+      tma_load_2d(&maps.a0l, &full_bar[s], st + 1 * PLANE, x, row0);
       if (NACC == 2) {
-        tma_load_2d(&maps.a1h, &full_bar[s], st + 2 * PLANE, x, ti * BM);
-        tma_load_2d(&maps.a1l, &full_bar[s], st + 3 * PLANE, x, ti * BM);
+        tma_load_2d(&maps.a1h, &full_bar[s], st + 2 * PLANE, x, row0);
+        tma_load_2d(&maps.a1l, &full_bar[s], st + 3 * PLANE, x, row0);
       }
-      tma_load_2d(&maps.bh, &full_bar[s], st + (2 * NACC) * PLANE, x, tj * BN);
-      tma_load_2d(&maps.bl, &full_bar[s], st + (2 * NACC + 1) * PLANE, x, tj * BN);
+      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * NACC * PLANE, x, col0);
+      tma_load_2d(&maps.bl, &full_bar[s], st + 2 * NACC * PLANE + C::B_PLANE, x, col0);
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    // ---- MMA issuer: K-tile kt puts its hi*hi products in hh buffer kt & 1 and its corrections in correction
+    // buffer g & 1, g = kt / CORR; tensor-memory columns [hh0 | hh1 | cr0 | cr1], ACC_COLS each
+    constexpr uint32_t idesc = idesc_bf16(BM, BNC);
     int kt = 0;
     for (; kt < k_tiles; ++kt) {
       const int s = kt % C::STAGES;
       const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      const int hb = kt & 1, g = kt / CORR, cb = g & 1;
+      const bool g_first = kt % CORR == 0;
+      // the drain must have read a buffer's previous contents before it is overwritten
+      if (kt >= 2 && !mbar_wait(&hh_empty[hb], (uint32_t)((kt >> 1) - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      if (g_first && g >= 2 && !mbar_wait(&cr_empty[cb], (uint32_t)((g >> 1) - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
       if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
         abort_flag = 1;
         break;
@@ -160,25 +198,93 @@ __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
-        const uint64_t bh = sdesc(base + (2 * NACC) * PLANE + ko), bl = sdesc(base + (2 * NACC + 1) * PLANE + ko);
-        const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+        const uint64_t bh = sdesc(base + 2 * NACC * PLANE + ko), bl = sdesc(base + 2 * NACC * PLANE + C::B_PLANE + ko);
 #pragma unroll
         for (int a = 0; a < NACC; ++a) {
           const uint64_t ah = sdesc(base + (2 * a) * PLANE + ko), al = sdesc(base + (2 * a + 1) * PLANE + ko);
-          const uint32_t d = tmem + a * BN;
-          umma(d, ah, bh, idesc, acc);
-          umma(d, ah, bl, idesc, 1u);
-          umma(d, al, bh, idesc, 1u);
+          const uint32_t dh = tmem + (uint32_t)(hb * C::ACC_COLS + a * BNC);
+          const uint32_t dc = tmem + (uint32_t)((2 + cb) * C::ACC_COLS + a * BNC);
+          umma(dh, ah, bh, idesc, kk > 0 ? 1u : 0u);
+          umma(dc, ah, bl, idesc, (g_first && kk == 0) ? 0u : 1u);
+          umma(dc, al, bh, idesc, 1u);
         }
       }
       umma_commit(&empty_bar[s]);
+      umma_commit(&hh_full[hb]);
+      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) umma_commit(&cr_full[cb]);
     }
     consumed = kt;
     umma_commit(&done_bar);   // arrives once every MMA issued above has completed
+  } else if (warp >= 4) {
+    // ---- drain: two warpgroups; group g (warps 4 + 4g .. 7 + 4g) sums columns [64 g, 64 g + 64) of every
+    // accumulator set (real: tile columns; complex: g = 0 the real, g = 1 the imaginary part) into FP32 running
+    // sums with round-to-nearest adds; warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the tile rows it owns
+    const int g = (warp - 4) >> 2, q = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    constexpr int HALF = C::ACC_COLS / 2;
+    float run[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) run[j] = 0.f;
+    bool ok = true;
+    // adds accumulator set `set` (0, 1: hi*hi buffers; 2, 3: correction buffers) into the running sums
+    auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, int set) {
+      if (!__all_sync(0xffffffffu, mbar_wait(full, parity, &abort_flag))) return false;
+      tc_fence_after();
+      tmem_add64(tmem + lane_base + (uint32_t)(set * C::ACC_COLS + g * HALF), run);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty);
+      return true;
+    };
+    for (int kt = 0; kt < k_tiles && ok; ++kt) {
+      const int hb = kt & 1, gr = kt / CORR, cb = gr & 1;
+      ok = drain(&hh_full[hb], &hh_empty[hb], (uint32_t)(kt >> 1) & 1u, hb);
+      if (ok && (kt % CORR == CORR - 1 || kt == k_tiles - 1))
+        ok = drain(&cr_full[cb], &cr_empty[cb], (uint32_t)(gr >> 1) & 1u, 2 + cb);
+    }
+    if (!ok) abort_flag = 1;
+    drain_bar();   // every drain warp is done (a timeout in one ends the others' bounded waits too)
+    if (!abort_flag) {
+      // The last accumulator's commit means every MMA has completed and every operand stage has been consumed, so
+      // the operand ring is free: the tile is staged there (row stride ACC_COLS + 1 floats: conflict-free both
+      // ways) and written out as coalesced row segments.
+      constexpr int LDS = C::ACC_COLS + 1;
+      float* stg = reinterpret_cast<float*>(smem);
+#pragma unroll
+      for (int j = 0; j < HALF; ++j) stg[(q * 32 + lane) * LDS + g * HALF + j] = run[j];
+      drain_bar();
+      // real: this warp's 32 rows, columns [64 g, 64 g + 64); complex: 16 of its rows, all 64 columns
+      const int r_lo = NACC == 1 ? 0 : 16 * g, r_hi = NACC == 1 ? 32 : 16 * g + 16;
+      const int c_lo = NACC == 1 ? g * HALF : 0;
+      for (int rr = r_lo; rr < r_hi; ++rr) {
+        const int row = row0 + q * 32 + rr;
+        if (row >= n) break;
+        const float* src = stg + (q * 32 + rr) * LDS;
+        for (int j = c_lo + lane; j < c_lo + HALF; j += 32) {
+          const int col = col0 + j;
+          if (col > row || col >= n) continue;
+          const double diag = col == row ? 1.0 : 0.0;
+          if constexpr (NACC == 1) {
+            reinterpret_cast<double*>(A_out)[(long)row * n + col] = diag + (double)src[j];
+            if (negpi32) negpi32[(long)row * n + col] = src[j];   // -Pi in FP32 for the Pi O product
+          } else {
+            reinterpret_cast<cplx*>(A_out)[(long)row * n + col] = mkc(diag + (double)src[j], (double)src[BNC + j]);
+          }
+        }
+      }
+      if (NACC == 1 && negpi32) {
+        // the transposed (upper) entries: the 32 lanes hold consecutive rows, so every store is coalesced
+        const int row = row0 + q * 32 + lane;
+        for (int j = c_lo; j < c_lo + HALF; ++j) {
+          const int col = col0 + j;
+          if (row < n && col < row) negpi32[(long)col * n + row] = stg[(q * 32 + lane) * LDS + j];
+        }
+      }
+    }
   }
   __syncwarp();
 
-  // ---- epilogue: warp w reads accumulator lanes 32w..32w+31 = rows of the tile
+  // every MMA issued has completed before the tensor memory is released, on every path
   const bool done_ok = mbar_wait(&done_bar, 0, nullptr);
   tc_fence_after();
   __syncthreads();
@@ -188,47 +294,6 @@ __global__ void __launch_bounds__(128, 1) tc_syrk_kernel(const __grid_constant__
       // drain loads that were issued but never consumed, so no copy lands after the CTA exits
       for (int kt = consumed; kt < issued; ++kt)
         mbar_wait(&full_bar[kt % C::STAGES], (uint32_t)(kt / C::STAGES) & 1u, nullptr);
-    }
-  }
-  if (done_ok && !abort_flag) {
-    const int row = ti * BM + warp * 32 + lane;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t v0[32], v1[32];
-      tmem_ld32(tmem + lane_base + c0, v0);
-      if (NACC == 2) tmem_ld32(tmem + lane_base + BN + c0, v1);
-      const int col0 = tj * BN + c0;
-      if (row < n) {
-        if (NACC == 1) {
-          double* Ar = reinterpret_cast<double*>(A_out) + (long)row * n;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = col0 + j;
-            if (col <= row && col < n) Ar[col] = (col == row ? 1.0 : 0.0) + (double)__uint_as_float(v0[j]);
-          }
-          if (negpi32) {   // -Pi in FP32, both triangles, for the Pi O product of the W solves
-            float* Pr = negpi32 + (long)row * n;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int col = col0 + j;
-              if (col <= row && col < n) {
-                Pr[col] = __uint_as_float(v0[j]);
-                // transposed entry: the 32 lanes hold consecutive rows, so this store is coalesced
-                if (col < row) negpi32[(long)col * n + row] = __uint_as_float(v0[j]);
-              }
-            }
-          }
-        } else {
-          cplx* Ac = reinterpret_cast<cplx*>(A_out) + (long)row * n;
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = col0 + j;
-            if (col <= row && col < n)
-              Ac[col] = mkc((col == row ? 1.0 : 0.0) + (double)__uint_as_float(v0[j]), (double)__uint_as_float(v1[j]));
-          }
-        }
-      }
     }
   }
   tc_fence_before();
@@ -357,12 +422,12 @@ Scratch carve(const void* shared, void* lane, int n, long n_ov) {
   return s;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int rows, long kpad) {
+bool make_map(CUtensorMap* m, const void* base, int rows, long kpad, int box_rows = BM) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BM};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -381,13 +446,13 @@ cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, float* n
   Maps maps;
   memset(&maps, 0, sizeof(maps));
   bool ok = make_map(&maps.a0h, s.s0h, n, s.kpad) && make_map(&maps.a0l, s.s0l, n, s.kpad) &&
-            make_map(&maps.bh, s.bh, n, s.kpad) && make_map(&maps.bl, s.bl, n, s.kpad);
+            make_map(&maps.bh, s.bh, n, s.kpad, C::BN) && make_map(&maps.bl, s.bl, n, s.kpad, C::BN);
   if (NACC == 2) ok = ok && make_map(&maps.a1h, s.s1h, n, s.kpad) && make_map(&maps.a1l, s.s1l, n, s.kpad);
   if (!ok) return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel<NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
   const int nt = (n + BM - 1) / BM;
-  tc_syrk_kernel<NACC><<<nt * (nt + 1) / 2, 128, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, negpi32,
-                                                                  ctx->d_status);
+  const int tiles = nt * (nt + 1) / 2 * (BM / C::BN);     // complex: two 128 x 64 halves per triangle tile
+  tc_syrk_kernel<NACC><<<tiles, 384, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, negpi32, ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }

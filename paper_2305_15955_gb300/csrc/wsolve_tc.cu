@@ -33,21 +33,29 @@ constexpr int PLANE = BM * BK * 2;       // bytes of one 128 x 64 BF16 tile
 constexpr int STAGES = 3;
 constexpr int STAGE = 4 * PLANE;         // A hi, A lo, B hi, B lo
 constexpr int SMEM = STAGES * STAGE + 1024;
-constexpr int TMEM_COLS = 128;
+constexpr int CORR = 8;            // K-tiles per correction accumulator (see tc_gemm_kernel)
+constexpr int TMEM_COLS = 4 * BN;  // hi*hi and corrections, two buffers each
 
 struct GemmMaps {
   CUtensorMap ah, al, bh, bl;
 };
 
 // out[(col) * ld + row_off + row] (=, -=) sum_k A[a_y0 + row][a_x0 + k] B[b_y0 + col][k],  row < M, col < N.
+// The tensor cores' FP32 accumulation loses a fraction of an ulp towards zero at every instruction, a bias over
+// long chains (the Pi O product runs over K = N_aux), so the hi*hi products of every K-tile go to a fresh
+// accumulator and the hi*lo + lo*hi corrections to one refreshed every CORR K-tiles (both double-buffered in tensor
+// memory), and warps 4-11 (two warpgroups, half the columns each) add every finished accumulator into FP32
+// running sums with round-to-nearest adds.  Warp 0 lane 0 drives TMA, warp 1 owns the tensor memory and lane 0
+// issues the MMAs, warps 2-3 are idle.
 template <bool SUB>
-__global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ GemmMaps maps, int M, int N,
+__global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__ GemmMaps maps, int M, int N,
                                                          int k_tiles, int a_x0, int a_y0, int b_y0, float* out,
                                                          long ld, int row_off, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t hh_full[2], hh_empty[2], cr_full[2], cr_empty[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -60,6 +68,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&hh_full[b], 1);
+      mbar_init(&hh_empty[b], 8);
+      mbar_init(&cr_full[b], 1);
+      mbar_init(&cr_empty[b], 8);
     }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -102,60 +116,98 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     for (; kt < k_tiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
+      const int hb = kt & 1, g = kt / CORR, cb = g & 1;
+      const bool g_first = kt % CORR == 0;
+      if (kt >= 2 && !mbar_wait(&hh_empty[hb], (uint32_t)((kt >> 1) - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      if (g_first && g >= 2 && !mbar_wait(&cr_empty[cb], (uint32_t)((g >> 1) - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
       if (!mbar_wait(&full_bar[s], ph, &abort_flag)) {
         abort_flag = 1;
         break;
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * STAGE);
+      const uint32_t dh = tmem + (uint32_t)(hb * BN), dc = tmem + (uint32_t)((2 + cb) * BN);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t ko = kk * 32;
         const uint64_t ah = sdesc(base + 0 * PLANE + ko), al = sdesc(base + 1 * PLANE + ko);
         const uint64_t bh = sdesc(base + 2 * PLANE + ko), bl = sdesc(base + 3 * PLANE + ko);
-        umma(tmem, ah, bh, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
-        umma(tmem, ah, bl, idesc, 1u);
-        umma(tmem, al, bh, idesc, 1u);
+        umma(dh, ah, bh, idesc, kk > 0 ? 1u : 0u);
+        umma(dc, ah, bl, idesc, (g_first && kk == 0) ? 0u : 1u);
+        umma(dc, al, bh, idesc, 1u);
       }
       umma_commit(&empty_bar[s]);
+      umma_commit(&hh_full[hb]);
+      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) umma_commit(&cr_full[cb]);
     }
     consumed = kt;
     umma_commit(&done_bar);
+  } else if (warp >= 4) {
+    // two drain warpgroups: group g sums columns [64 g, 64 g + 64); warp w reads lanes 32 (w % 4) .. + 31 = rows
+    const int g = (warp - 4) >> 2, q = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float run[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) run[j] = 0.f;
+    bool ok = true;
+    // adds accumulator set `set` (0, 1: hi*hi buffers; 2, 3: correction buffers) into the running sums
+    auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, int set) {
+      if (!__all_sync(0xffffffffu, mbar_wait(full, parity, &abort_flag))) return false;
+      tc_fence_after();
+      tmem_add64(tmem + lane_base + (uint32_t)(set * BN + g * 64), run);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty);
+      return true;
+    };
+    for (int kt = 0; kt < k_tiles && ok; ++kt) {
+      const int hb = kt & 1, gr = kt / CORR, cb = gr & 1;
+      ok = drain(&hh_full[hb], &hh_empty[hb], (uint32_t)(kt >> 1) & 1u, hb);
+      if (ok && (kt % CORR == CORR - 1 || kt == k_tiles - 1))
+        ok = drain(&cr_full[cb], &cr_empty[cb], (uint32_t)(gr >> 1) & 1u, 2 + cb);
+    }
+    if (!ok) {
+      abort_flag = 1;
+    } else {
+      // out is column-major (out[col][row]): the 32 lanes hold consecutive rows, so every access is coalesced
+      const int row = tm * BM + q * 32 + lane;
+      if (row < M) {
+        float* o = out + row_off + row;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          // every load of 32 columns before any store: the compiler cannot prove o[j ld] and o[k ld] distinct
+          float cur[32];
+          if (SUB) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int col = tn * BN + g * 64 + c0 + j;
+              cur[j] = col < N ? o[(long)col * ld] : 0.f;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int col = tn * BN + g * 64 + c0 + j;
+            if (col < N) o[(long)col * ld] = SUB ? cur[j] - run[c0 + j] : run[c0 + j];
+          }
+        }
+      }
+    }
   }
   __syncwarp();
 
+  // every MMA issued has completed before the tensor memory is released, on every path
   const bool done_ok = mbar_wait(&done_bar, 0, nullptr);
   tc_fence_after();
   __syncthreads();
   if (threadIdx.x == 0 && (!done_ok || abort_flag)) {
     raise_status(status, DEV_ERR_TIMEOUT);
     for (int kt = consumed; kt < issued; ++kt) mbar_wait(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, nullptr);
-  }
-  if (done_ok && !abort_flag) {
-    const int row = tm * BM + warp * 32 + lane;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + lane_base + c0, v);
-      if (row < M) {
-        float* o = out + row_off + row;
-        // every load of the chunk before any store: the compiler cannot prove o[j ld] and o[k ld] distinct
-        float cur[32];
-        if (SUB) {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int col = tn * BN + c0 + j;
-            cur[j] = col < N ? o[(long)col * ld] : 0.f;
-          }
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = tn * BN + c0 + j;
-          if (col < N) o[(long)col * ld] = SUB ? cur[j] - __uint_as_float(v[j]) : __uint_as_float(v[j]);
-        }
-      }
-    }
   }
   tc_fence_before();
   __syncthreads();
@@ -493,7 +545,7 @@ cdwac_status gemm(cdwac_ctx* ctx, const GemmMaps& maps, int M, int N, int k_tile
   if (M <= 0 || N <= 0) return CDWAC_OK;
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_gemm_kernel<SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-  tc_gemm_kernel<SUB><<<mt * nt, 128, SMEM, st>>>(maps, M, N, k_tiles, a_x0, a_y0, 0, out, ld, row_off,
+  tc_gemm_kernel<SUB><<<mt * nt, 384, SMEM, st>>>(maps, M, N, k_tiles, a_x0, a_y0, 0, out, ld, row_off,
                                                   ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;

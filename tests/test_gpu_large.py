@@ -3,13 +3,17 @@ of CTAs on the GPU (N_aux = 2200: 18 row tiles, 171 lower-triangle tiles for 152
 N_ov = 32 400 with a ragged K tail), against the oracle on a few frequencies.
 
 FP64 path: W(i xi) and W(z) to FP64 rounding.  Mixed path: the tolerance of every table row is derived from the
-split-BF16 error of Pi and the conditioning of I - Pi at that frequency.  With hi = bf16(x) and lo = bf16(x - hi) an
-FP32 operand keeps x - hi - lo <= 2^-17 |x|; the dropped lo*lo product is <= 2^-18 |x y|; the weighted operand
-S = fp32(w) * x adds two FP32 roundings (2^-24 each) and the FP32 accumulation of the tensor cores adds at most
-about log2(K) * 2^-24 per term for a tree-blocked sum.  So every term of Pi_PQ = sum_k S_Pk B_Qk carries at most
-u = 2^-15 of |S_Pk B_Qk| and |dPi| <= u |S| |B|^T elementwise.  A first-order perturbation bound for
-W = o^T (I - Pi)^-1 Pi o then gives |dW| <= ||(I - Pi)^-1||_2^2 ||u |S| |B|^T||_2 ||o||^2, which the test evaluates
-with the oracle's own matrices (FP64) and multiplies by a safety factor of 4.
+split-BF16 error of Pi and the conditioning of I - Pi at that frequency.  With hi = bf16(x) and lo = bf16(x - hi)
+an FP32 operand keeps x - hi - lo <= 2^-17 |x|, the dropped lo*lo product is <= 2^-18 |x y|, and the weighted
+operand S = fp32(w) * x adds two FP32 roundings: every term S_Pk B_Qk of Pi carries a relative error below
+2^-16, with signs that vary from term to term (the tensor-core accumulation runs in chunks of 128 columns summed
+with round-to-nearest, so it adds no bias), and the normwise error of Pi is taken as 2^-16 ||Pi||_2.  The W solves'
+split-BF16 products and FP32 block solves act as a backward error of the same size on the factor.  Together
+u = 2^-15 of ||I - Pi||_2, and first-order perturbation of W_nm = o_m^T [(I - Pi)^-1 - I] o_m bounds
+|dW_nm| <= u kappa(I - Pi) ||(I - Pi)^-1||_2 ||o_m||^2 with kappa the 2-norm condition number, which the test
+evaluates from the oracle's matrices (FP64) with a safety factor of 4.  Near-real points
+among the excitations (kappa ~ 1e4 and more) get a correspondingly loose tolerance; the imaginary axis (kappa of
+order ||Pi||) is held to a fraction of W's size.
 """
 import numpy as np
 import pytest
@@ -54,19 +58,12 @@ def _oracle_tables(spec, eps, B, On, xi, zr):
 
 
 def _w_bound(B, D, On, z, m_idx):
-    """Per-state first-order bound on |dW_nm| over m_idx from a BF16x3 Pi (see the module docstring)."""
-    z = complex(z)
-    if z.real == 0.0:
-        w = -4.0 * D / (z.imag ** 2 + D ** 2)
-    else:
-        w = 4.0 * D / (z * z - D * D)
-    absB = np.abs(B)
-    E = U_BF16X3 * ((absB * np.abs(w)[None, :]) @ absB.T)
-    A = np.eye(B.shape[0]) - o.polarizability(B, D, z)
-    inv_norm = 1.0 / np.linalg.svd(A, compute_uv=False)[-1]
-    e_norm = np.linalg.norm(E, 2)
+    """Per-state bound on |dW_nm| over m_idx from a BF16x3 Pi and its condition number (module docstring)."""
+    A = np.eye(B.shape[0]) - o.polarizability(B, D, complex(z))
+    sv = np.linalg.svd(A, compute_uv=False)
+    kappa, inv_norm = sv[0] / sv[-1], 1.0 / sv[-1]
     on2 = np.sum(On[:, :, m_idx] ** 2, axis=1)                      # [n_states, len(m_idx)]
-    return SAFETY * inv_norm ** 2 * e_norm * on2, inv_norm * np.linalg.norm(A, 2)
+    return SAFETY * U_BF16X3 * kappa * inv_norm * on2, kappa
 
 
 def test_fp64_path_at_multi_wave_size(ctx, system):
@@ -97,13 +94,13 @@ def test_mixed_path_at_multi_wave_size_within_derived_bound(ctx, system):
     Wg, Wrg = W.cpu().numpy(), pade.W_real.cpu().numpy()
     m_all = np.arange(spec.n_basis)
     for k, x in enumerate(xi_h):
-        bound, cond = _w_bound(B, D, On, 1j * x, m_all)
+        bound, kappa = _w_bound(B, D, On, 1j * x, m_all)
         err = np.abs(Wg[:, k, :] - Wim[:, k, :])
-        assert np.all(err <= bound), (k, cond, float((err / bound).max()))
-        # the bound is not vacuous: W is resolved to well under its size on the imaginary axis
-        assert np.all(bound < 1e-2 * np.abs(Wim[:, k, :]).max(axis=1, keepdims=True))
+        assert np.all(err <= bound), (k, kappa, float((err / bound).max()))
+        # the bound is not vacuous: on the imaginary axis it holds W to a fraction of its size
+        assert np.all(bound.max(axis=1) < 0.05 * np.abs(Wim[:, k, :]).max(axis=1)), (k, kappa)
     m_occ = np.arange(spec.n_occ)
     for j, z in enumerate(zr):
-        bound, cond = _w_bound(B, D, On, z, m_occ)
+        bound, kappa = _w_bound(B, D, On, z, m_occ)
         err = np.abs(Wrg[:, j, :] - Wre[:, j, :])
-        assert np.all(err <= bound), (j, z, cond, float((err / bound).max()))
+        assert np.all(err <= bound), (j, z, kappa, float((err / bound).max()))
