@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["acene", "medium", "small", "batch", "acarbon"], default="acene")
     ap.add_argument("--batch-systems", type=int, default=16, help="systems in the batch workload")
+    ap.add_argument("--qp-max-iter", type=int, default=100,
+                    help="fixed-point iterations of the QP solve before the bisection fallback (100 = the method's)")
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-extras", action="store_true", help="skip e2e, plain-CD and CPU-baseline measurements")
     ap.add_argument("--n-imag", type=int, default=100, help="imaginary grid points (100 = the workload's value)")
@@ -578,10 +580,12 @@ def run_batch(args, rank, ws, dist):
     res = [cdwac.BatchResult(s, prm, omega, omega, dev) for s in systems]
     lanes = 4
     l0 = ctx.launch_count()
-    (ln, la), items = cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True)   # eager run + capture
+    (ln, la), items = cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True,   # eager run + capture
+                                      max_iter=args.qp_max_iter)
     graph_kernels = (ctx.launch_count() - l0) // 2   # the eager run and the capture enqueue the same kernels
     for _ in range(max(0, args.warmup - 1)):
-        cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True, items=items, sync=False)
+        cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True, items=items, sync=False,
+                        max_iter=args.qp_max_iter)
     torch.cuda.synchronize()
     barrier(dist)
     stream = torch.cuda.current_stream()
@@ -590,7 +594,8 @@ def run_batch(args, rank, ws, dist):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True, items=items, sync=False)
+            cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True, items=items, sync=False,
+                            max_iter=args.qp_max_iter)
         e1.record(stream)
         torch.cuda.synchronize()
     ctx.sync_status((cdwac.ERR_PADE_BREAKDOWN, cdwac.ERR_QP_NOT_CONVERGED))
@@ -605,7 +610,7 @@ def run_batch(args, rank, ws, dist):
             "config": {"workload": f"uneven batch: {len(specs)} systems, N_basis " +
                                    ",".join(str(sp.n_basis) for sp in specs) +
                                    ", N_aux = 3.3 N_basis, 4 core states each, one CUDA graph per step",
-                       "lanes": ln, "lookahead": la, "n_states_total": n_states,
+                       "lanes": ln, "lookahead": la, "n_states_total": n_states, "qp_max_iter": args.qp_max_iter,
                        "input_generation_s": t_gen},
             "pi_tflop_per_step": pi_flops / 1e12,
             "gpu_launches": int(graph_kernels), "gpu_launches_note": "kernel nodes of the CUDA graph replayed per step",

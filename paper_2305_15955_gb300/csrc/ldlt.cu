@@ -37,6 +37,27 @@ __device__ inline cplx shfl_xor_T(cplx v, int m) {
   return mkc(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
+// 1/d by Newton's iteration x <- x + x (1 - d x), started from the single-precision reciprocal of d: each step
+// squares the relative error, so two steps take the 2^-23 start to the FP64 rounding level (the last step's
+// rounding leaves x within an ulp or so of 1/d; the factorisation tests bound the result through its backward
+// error).  Four FP64 FMAs and two conversions: GB300 issues one FP64 warp instruction in about 64 cycles, and the
+// pivot reciprocal is on the factorisation's critical path.  Outside single precision's exponent range (|d|
+// beyond 2^+-99) the division.
+__device__ inline double rcp_T(double d) {
+  const int E = (int)(((unsigned long long)__double_as_longlong(d) >> 52) & 0x7FF);
+  if (E < 1023 - 99 || E > 1023 + 99) return 1.0 / d;
+  double x = (double)__frcp_rn((float)d);
+  double e = fma(-d, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-d, x, 1.0);
+  return fma(x, e, x);
+}
+// 1/z = conj(z) / |z|^2 with the reciprocal above
+__device__ inline cplx rcp_T(cplx z) {
+  const double r = rcp_T(fma(z.x, z.x, z.y * z.y));
+  return mkc(z.x * r, -z.y * r);
+}
+
 __device__ inline double shfl_T(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ inline cplx shfl_T(cplx v, int src) {
   return mkc(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
@@ -91,7 +112,7 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
       if (tid == 0) bad_step = bad ? 1 : 0;
       // one reciprocal per warp, broadcast (FP64 division is a multi-instruction sequence on the scarce FP64 units)
       T rinv = N::one();
-      if ((tid & 31) == 0) rinv = N::div(N::one(), bad ? N::one() : d0);
+      if ((tid & 31) == 0) rinv = bad ? N::one() : rcp_T(d0);
       rinv = shfl_T(rinv, 0);
       if (tid > j && tid < nb) {
         const T u = S[tid * SD + j];
@@ -118,7 +139,7 @@ __global__ void __launch_bounds__(256) diag_kernel(T* A, int n, int k0, T* dinv,
     const int i = e / NB, j = e % NB;
     if (i < nb && j <= i) A[(long)(k0 + i) * n + (k0 + j)] = S[i * SD + j];   // diagonal holds d_i
   }
-  if (tid < nb) dinv[k0 + tid] = N::div(N::one(), S[tid * SD + tid]);
+  if (tid < nb) dinv[k0 + tid] = rcp_T(S[tid * SD + tid]);
 }
 
 // ---- inverses of the unit-lower diagonal blocks, for the solves after the factorisation ------------------------

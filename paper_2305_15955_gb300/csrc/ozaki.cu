@@ -8,14 +8,16 @@
 //
 //   * every row x of W and of L is scaled by 2^-e, e the exponent of its largest magnitude, and cut into S signed
 //     integer digits of B bits: x 2^-e = sum_s d_s 2^-Bs + r, |d_1| <= 2^B, |d_s| <= 2^(B-1) for s > 1,
-//     |r| <= 2^-57.  Real: S = 7, B = 8; complex: S = 8, B = 7.  Each digit is exact in BF16 and each digit
-//     product is exact in FP32.
+//     |r| <= 2^-57 (the rounding of x 2^-e to SB fractional bits; the digits are then exact).  Real: S = 7, B = 8;
+//     complex: S = 8, B = 7.  Each digit is exact in BF16 and each digit product is exact in FP32.  The digits are
+//     cut with integer arithmetic from the bit patterns: GB300's FP64 units are its scarcest resource.
 //   * tcgen05.mma sums, for each level L = s + t (S(S+1)/2 digit pairs), the products over the panel columns in
 //     its own FP32 tensor-memory accumulator.  All partial sums of one level are integers of magnitude below
 //     64 x 147 456 < 2^24 (real, largest level) or 128 x 40 960 < 2^23 (complex, K = 128), so every
 //     accumulation is exact.
 //   * the epilogue forms sum_L 2^-BL acc_L exactly in 64-bit integers (GB300's FP64 units are the scarce
-//     resource), converts it once to FP64, scales it by 2^(e_i + e_j) and subtracts it from A (one FMA).
+//     resource), converts it once to FP64, scales it by 2^(e_i + e_j) with an integer add to the exponent field
+//     and subtracts it from A.
 //
 // The digits dropped (levels above S + 1 and the remainders r) are below about 2^-54 max|W_i| max|L_j| per
 // column, the size of the rounding error of an FP64 dot product of this length.
@@ -71,6 +73,14 @@ struct OzMaps {
   CUtensorMap w, l;
 };
 
+// RN(a) 2^k as an FP64 number: the hardware conversion of a (round to nearest), then the power of two applied to
+// the exponent field with an integer add instead of an FP64 multiply (GB300 issues an FP64 warp instruction in about
+// 64 cycles).  Exact as long as the result stays in the normal range, which these updates do.
+__device__ inline double scaled_int64(long long a, int k) {
+  const long long b = __double_as_longlong(__ll2double_rn(a));
+  return __longlong_as_double((b & 0x7FF0000000000000ll) ? b + ((long long)k << 52) : b);
+}
+
 template <bool CPLX>
 __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
                                                            int k1, const int* __restrict__ ew,
@@ -98,7 +108,7 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
   __shared__ int loads_issued;
-  __shared__ double scale_w[BM], scale_l[BN];
+  __shared__ int exp_w[BM], exp_l[BN];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
@@ -110,8 +120,8 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
     loads_issued = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int r = threadIdx.x; r < BM; r += blockDim.x) scale_w[r] = row0 + r < n ? ldexp(1.0, ew[row0 + r]) : 0.0;
-  for (int c = threadIdx.x; c < BN; c += blockDim.x) scale_l[c] = col0 + c < n ? ldexp(1.0, el[col0 + c]) : 0.0;
+  for (int r = threadIdx.x; r < BM; r += blockDim.x) exp_w[r] = row0 + r < n ? ew[row0 + r] : 0;
+  for (int c = threadIdx.x; c < BN; c += blockDim.x) exp_l[c] = col0 + c < n ? el[col0 + c] : 0;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"((uint32_t)C::TMEM_COLS)
@@ -212,8 +222,7 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
     }
     {
       // exact integer recombination N = sum_L acc_L 2^(SH - 7L) on the integer pipe (bits of the lowest levels
-      // below 2^-SH are rounded off, < 2^-60 of the largest term), then one conversion: two FP64 operations per
-      // element in all
+      // below 2^-SH are rounded off, < 2^-60 of the largest term)
       long long acc[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0;
@@ -229,9 +238,12 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
           acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> -sh);   // rounded, not floored
         }
       }
+      // staged: the scaled update N 2^(e_row + e_col - SHIFT) of element (tile row wq * 32 + lane, column c0 + j);
+      // the read-modify-write below is then one FP64 subtraction per element
       double* st = stage + ((wg * 4 + wq) * 32) * 33;
+      const int kr = exp_w[wq * 32 + lane] - C::SHIFT;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = __ll2double_rn(acc[j]);
+      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = scaled_int64(acc[j], kr + exp_l[c0 + j]);
     }
     if (CPLX)
       __syncthreads();   // both parts of every row staged
@@ -244,7 +256,6 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
         if (row < n && col <= row) cv1[rr] = Ab[(long)row * n + col];
       }
     }
-    const double sl = scale_l[c0 + lane] * ldexp(1.0, -C::SHIFT);   // exact: powers of two
     const double* st0 = stage + ((CPLX ? 0 : wg) * 4 + wq) * 32 * 33;
     const double* st1 = stage + (4 + wq) * 32 * 33;
     const int r_off = CPLX ? 16 * wg : 0;              // first staged row of this warp within its quarter
@@ -254,13 +265,12 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
       for (int rr = 0; rr < 16; ++rr) {
         const int r = r_off + h * 16 + rr, row = row0 + wq * 32 + r;
         if (row < n && col <= row) {
-          const double sc = scale_w[wq * 32 + r] * sl;
           T v = h == 0 ? cv0[rr] : cv1[rr];
           if constexpr (!CPLX) {
-            v = fma(-st0[r * 33 + lane], sc, v);
+            v = v - st0[r * 33 + lane];
           } else {
-            v.x = fma(-st0[r * 33 + lane], sc, v.x);
-            v.y = fma(-st1[r * 33 + lane], sc, v.y);
+            v.x = v.x - st0[r * 33 + lane];
+            v.y = v.y - st1[r * 33 + lane];
           }
           Ab[(long)row * n + col] = v;
         }
@@ -290,6 +300,39 @@ __device__ inline void load2(const cplx* p, double (&x)[2][2]) {
   x[1][1] = b.y;
 }
 
+// Fixed-point value round(|x| 2^(F - e)) of an FP64 number with the sign of x, for a row whose largest magnitude is
+// below 2^e (|result| < 2^F), from the bit pattern alone: GB300's FP64 pipe issues one warp instruction in about 64
+// cycles, its integer pipe one per cycle.  Zero and subnormal inputs give 0 (their size is far below 2^(e - F)).
+__device__ inline long long fixed_point(double x, int e, int F) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((b >> 52) & 0x7FF);
+  if (E == 0) return 0;
+  const long long mant = (long long)((b & 0xFFFFFFFFFFFFFull) | (1ull << 52));   // |x| = mant 2^(E - 1075)
+  const int sh = E - 1075 + F - e;                                                 // <= F - 53
+  long long v;
+  if (sh >= 0)
+    v = mant << sh;
+  else if (sh > -62)
+    v = (mant + (1ll << (-sh - 1))) >> -sh;                                        // rounded to nearest
+  else
+    v = 0;
+  return (b >> 63) ? -v : v;
+}
+
+// Signed digits of v (|v| < 2^F, F = S BETA): v = sum_s d_s 2^(F - BETA (s + 1)), d_0 the nearest integer to
+// v / 2^(F - BETA) and every later digit the nearest integer to what remains at its weight, so |d_0| <= 2^BETA,
+// |d_s| <= 2^(BETA - 1) and the last digit takes the exact remainder.
+template <int S, int BETA>
+__device__ inline void signed_digits(long long v, float (&d)[S]) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const int k = BETA * (S - 1 - s);
+    const long long q = k ? (v + (1ll << (k - 1))) >> k : v;
+    d[s] = (float)q;   // |q| <= 2^BETA: exact
+    v -= q * (1ll << k);
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const T* __restrict__ A, int n, int k0,
                                                        const T* __restrict__ wpanel, __nv_bfloat16* __restrict__ wpl,
@@ -305,27 +348,28 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const T* __restrict__ A, 
   const T* src = op == 0 ? wpanel + (long)row * K : A + (long)row * n + k0;
   double x[2][2];
   load2(src + 2 * lane, x);
-  double m = 0.0;
+  // largest magnitude of the row: the bit patterns of non-negative doubles order like the numbers
+  unsigned long long m = 0;
 #pragma unroll
-  for (int p = 0; p < NPART; ++p) m = fmax(m, fmax(fabs(x[p][0]), fabs(x[p][1])));
+  for (int p = 0; p < NPART; ++p)
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);   // m < 2^e, so every scaled entry lies in (-1, 1)
+    for (int c = 0; c < 2; ++c)
+      m = max(m, (unsigned long long)__double_as_longlong(x[p][c]) & 0x7FFFFFFFFFFFFFFFull);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)m, o));
+  // e with max|x| < 2^e (the exponent frexp returns); 0 for an all-zero row
+  const int e = m ? (int)(m >> 52) - 1022 : 0;
   __nv_bfloat16* pl = op == 0 ? wpl : lpl;
 #pragma unroll
   for (int p = 0; p < NPART; ++p) {
-    double y0 = ldexp(x[p][0], -e), y1 = ldexp(x[p][1], -e);
+    float d0[S], d1[S];
+    signed_digits<S, BETA>(fixed_point(x[p][0], e, S * BETA), d0);
+    signed_digits<S, BETA>(fixed_point(x[p][1], e, S * BETA), d1);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      y0 *= (double)(1 << BETA);
-      y1 *= (double)(1 << BETA);
-      const double d0 = rint(y0), d1 = rint(y1);
-      y0 -= d0;   // exact: the remainder of an FP64 number after its nearest integer
-      y1 -= d1;
       __nv_bfloat162 v;
-      v.x = __float2bfloat16_rn((float)d0);   // |d| <= 2^BETA: exact
-      v.y = __float2bfloat16_rn((float)d1);
+      v.x = __float2bfloat16_rn(d0[s]);
+      v.y = __float2bfloat16_rn(d1[s]);
       *reinterpret_cast<__nv_bfloat162*>(pl + ((size_t)(p * S + s) * n + row) * K + 2 * lane) = v;
     }
   }

@@ -12,8 +12,8 @@
 // 384 threads.  Warp 0 lane 0 drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory
 // stages; warp 1 owns the tensor memory and lane 0 issues tcgen05.mma (M = 128, N = 128 or 64, K = 16 per
 // instruction, both operands K-major); tcgen05.commit releases a stage when the MMAs reading it finish.  The hi*hi
-// products of every K-tile and the corrections of every 8 K-tiles go to fresh accumulators (double-buffered in
-// tensor memory); warps 4-11 read each finished one (tcgen05.ld 32x32b, the accumulator rows they own), add it
+// products of every K-tile (one buffer per operand stage, in turn) and the corrections of every 32 K-tiles go to
+// fresh accumulators in tensor memory; warps 4-11 read each finished one (tcgen05.ld 32x32b, the accumulator rows they own), add it
 // into FP32 running sums and at the end write A in FP64.  Every wait on an mbarrier is bounded (5 s): on expiry the kernel records
 // CDWAC_ERR_TIMEOUT, stops issuing, drains what it issued and frees its tensor memory.
 #include <cuda.h>
@@ -77,11 +77,12 @@ __device__ inline void grouped_tile_coords(int b, int nt, int& ti, int& tj) {
 // instruction that adds into an accumulator loses a fraction of an ulp of it, always towards zero.  Summed over all
 // K = 129 600 columns of the acene-like system (8100 K-steps of three products into one accumulator) Pi came out
 // about 1.2e-3 too small in magnitude, a bias that survives in W at large xi.  So the hi*hi products of every
-// K-tile (64 columns, a chain of four instructions) go to a fresh accumulator, and the hi*lo + lo*hi corrections
-// (2^-8 of the size: their chain bias is negligible) to a second one refreshed every CORR K-tiles; both are
-// double-buffered in tensor memory, and a drain warpgroup adds every finished accumulator into FP32 running sums
-// with round-to-nearest adds on the CUDA cores while the MMAs fill the other buffers.
-constexpr int CORR = 8;
+// K-tile (64 columns, a chain of four instructions) go to a fresh accumulator, one per operand stage in turn, and
+// the hi*lo + lo*hi corrections (2^-8 of the size, so a chain of 32 K-tiles biases Pi by less than 1e-7) to one
+// more refreshed every CORR K-tiles; the drain warps add every finished accumulator into FP32 running sums with
+// round-to-nearest adds on the CUDA cores while the MMAs fill the others.  The drain needs no commit of its own:
+// the one that frees a K-tile's operand stage also marks its accumulators complete.
+constexpr int CORR = 32;  // K-tiles per correction accumulator (one buffer)
 
 template <int NACC>
 struct Cfg {
@@ -91,7 +92,8 @@ struct Cfg {
   static constexpr int STAGES = NACC == 1 ? 3 : 2;
   static constexpr int SMEM = STAGES * STAGE + 1024;       // + alignment slack
   static constexpr int ACC_COLS = NACC * BN;               // tensor-memory columns of one accumulator set
-  static constexpr int TMEM_COLS = 4 * ACC_COLS;           // hi*hi and corrections, two buffers each: 512
+  static constexpr int NHH = STAGES;                       // hi*hi buffers, one per operand stage
+  static constexpr int TMEM_COLS = 4 * ACC_COLS;           // (NHH + 1) x ACC_COLS <= 512 columns
 };
 
 // A = I + S B^T (lower triangle).  NACC == 1: real A (double*), 128 x 128 tiles.  NACC == 2: complex A (cplx*),
@@ -103,11 +105,12 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
                                                          void* A_out, float* negpi32, unsigned* status) {
   using C = Cfg<NACC>;
   constexpr int BNC = C::BN;
+  constexpr int NHH = C::NHH;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[C::STAGES];
   __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
-  __shared__ __align__(8) uint64_t hh_full[2], hh_empty[2], cr_full[2], cr_empty[2];
+  __shared__ __align__(8) uint64_t hh_empty[NHH], cr_empty;
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -124,12 +127,8 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&hh_full[b], 1);
-      mbar_init(&hh_empty[b], 8);
-      mbar_init(&cr_full[b], 1);
-      mbar_init(&cr_empty[b], 8);
-    }
+    for (int b = 0; b < NHH; ++b) mbar_init(&hh_empty[b], 8);
+    mbar_init(&cr_empty, 8);
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     issued = 0;
@@ -171,21 +170,21 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: K-tile kt puts its hi*hi products in hh buffer kt & 1 and its corrections in correction
-    // buffer g & 1, g = kt / CORR; tensor-memory columns [hh0 | hh1 | cr0 | cr1], ACC_COLS each
+    // ---- MMA issuer: K-tile kt puts its hi*hi products in hh buffer kt % NHH and its corrections in the
+    // correction buffer (group g = kt / CORR); tensor-memory columns [hh0 | .. | hh(NHH-1) | cr], ACC_COLS each
     constexpr uint32_t idesc = idesc_bf16(BM, BNC);
     int kt = 0;
     for (; kt < k_tiles; ++kt) {
       const int s = kt % C::STAGES;
       const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
-      const int hb = kt & 1, g = kt / CORR, cb = g & 1;
+      const int hb = kt % NHH, g = kt / CORR;
       const bool g_first = kt % CORR == 0;
       // the drain must have read a buffer's previous contents before it is overwritten
-      if (kt >= 2 && !mbar_wait(&hh_empty[hb], (uint32_t)((kt >> 1) - 1) & 1u, &abort_flag)) {
+      if (kt >= NHH && !mbar_wait(&hh_empty[hb], (uint32_t)(kt / NHH - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
-      if (g_first && g >= 2 && !mbar_wait(&cr_empty[cb], (uint32_t)((g >> 1) - 1) & 1u, &abort_flag)) {
+      if (g_first && g >= 1 && !mbar_wait(&cr_empty, (uint32_t)(g - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
@@ -195,23 +194,30 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * C::STAGE);
+      // the hi*hi products of the K-tile first, then its corrections: consecutive instructions share an accumulator
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk) {
-        const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
-        const uint64_t bh = sdesc(base + 2 * NACC * PLANE + ko), bl = sdesc(base + 2 * NACC * PLANE + C::B_PLANE + ko);
+      for (int a = 0; a < NACC; ++a) {
+        const uint32_t dh = tmem + (uint32_t)(hb * C::ACC_COLS + a * BNC);
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) {
-          const uint64_t ah = sdesc(base + (2 * a) * PLANE + ko), al = sdesc(base + (2 * a + 1) * PLANE + ko);
-          const uint32_t dh = tmem + (uint32_t)(hb * C::ACC_COLS + a * BNC);
-          const uint32_t dc = tmem + (uint32_t)((2 + cb) * C::ACC_COLS + a * BNC);
-          umma(dh, ah, bh, idesc, kk > 0 ? 1u : 0u);
-          umma(dc, ah, bl, idesc, (g_first && kk == 0) ? 0u : 1u);
-          umma(dc, al, bh, idesc, 1u);
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
+          umma(dh, sdesc(base + (2 * a) * PLANE + ko), sdesc(base + 2 * NACC * PLANE + ko), idesc,
+               kk == 0 ? 0u : 1u);
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) {
+        const uint32_t dc = tmem + (uint32_t)(NHH * C::ACC_COLS + a * BNC);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t ko = kk * 32;
+          const uint64_t bh = sdesc(base + 2 * NACC * PLANE + ko), bl = sdesc(base + 2 * NACC * PLANE + C::B_PLANE + ko);
+          umma(dc, sdesc(base + (2 * a) * PLANE + ko), bl, idesc, (g_first && kk == 0) ? 0u : 1u);
+          umma(dc, sdesc(base + (2 * a + 1) * PLANE + ko), bh, idesc, 1u);
         }
       }
       umma_commit(&empty_bar[s]);
-      umma_commit(&hh_full[hb]);
-      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) umma_commit(&cr_full[cb]);
+
     }
     consumed = kt;
     umma_commit(&done_bar);   // arrives once every MMA issued above has completed
@@ -226,9 +232,8 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
 #pragma unroll
     for (int j = 0; j < HALF; ++j) run[j] = 0.f;
     bool ok = true;
-    // adds accumulator set `set` (0, 1: hi*hi buffers; 2, 3: correction buffers) into the running sums
-    auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, int set) {
-      if (!__all_sync(0xffffffffu, mbar_wait(full, parity, &abort_flag))) return false;
+    // adds accumulator set `set` (0 .. NHH - 1: hi*hi buffers; NHH: the correction buffer) into the running sums
+    auto drain = [&](uint64_t* empty, int set) {
       tc_fence_after();
       tmem_add64(tmem + lane_base + (uint32_t)(set * C::ACC_COLS + g * HALF), run);
       tc_fence_before();
@@ -237,10 +242,14 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
       return true;
     };
     for (int kt = 0; kt < k_tiles && ok; ++kt) {
-      const int hb = kt & 1, gr = kt / CORR, cb = gr & 1;
-      ok = drain(&hh_full[hb], &hh_empty[hb], (uint32_t)(kt >> 1) & 1u, hb);
-      if (ok && (kt % CORR == CORR - 1 || kt == k_tiles - 1))
-        ok = drain(&cr_full[cb], &cr_empty[cb], (uint32_t)(gr >> 1) & 1u, 2 + cb);
+      // the commit that releases K-tile kt's operand stage arrives once every MMA up to kt has completed, so its
+      // phase also marks the K-tile's accumulators complete; the MMAs of K-tile kt + STAGES, whose commit ends the
+      // stage's next phase, wait for this drain (NHH = STAGES), so the phase cannot pass unobserved
+      const uint32_t parity = (uint32_t)(kt / C::STAGES) & 1u;
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[kt % C::STAGES], parity, &abort_flag));
+      if (!ok) break;
+      drain(&hh_empty[kt % NHH], kt % NHH);
+      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) drain(&cr_empty, NHH);
     }
     if (!ok) abort_flag = 1;
     drain_bar();   // every drain warp is done (a timeout in one ends the others' bounded waits too)

@@ -33,8 +33,9 @@ constexpr int PLANE = BM * BK * 2;       // bytes of one 128 x 64 BF16 tile
 constexpr int STAGES = 3;
 constexpr int STAGE = 4 * PLANE;         // A hi, A lo, B hi, B lo
 constexpr int SMEM = STAGES * STAGE + 1024;
-constexpr int CORR = 8;            // K-tiles per correction accumulator (see tc_gemm_kernel)
-constexpr int TMEM_COLS = 4 * BN;  // hi*hi and corrections, two buffers each
+constexpr int NHH = STAGES;        // hi*hi accumulator buffers, one per operand stage (see tc_gemm_kernel)
+constexpr int CORR = 32;           // K-tiles per correction accumulator (one buffer)
+constexpr int TMEM_COLS = 4 * BN;  // three hi*hi buffers and the corrections
 
 struct GemmMaps {
   CUtensorMap ah, al, bh, bl;
@@ -43,8 +44,7 @@ struct GemmMaps {
 // out[(col) * ld + row_off + row] (=, -=) sum_k A[a_y0 + row][a_x0 + k] B[b_y0 + col][k],  row < M, col < N.
 // The tensor cores' FP32 accumulation loses a fraction of an ulp towards zero at every instruction, a bias over
 // long chains (the Pi O product runs over K = N_aux), so the hi*hi products of every K-tile go to a fresh
-// accumulator and the hi*lo + lo*hi corrections to one refreshed every CORR K-tiles (both double-buffered in tensor
-// memory), and warps 4-11 (two warpgroups, half the columns each) add every finished accumulator into FP32
+// accumulator (three in turn) and the hi*lo + lo*hi corrections to one refreshed every CORR K-tiles, and warps 4-11 (two warpgroups, half the columns each) add every finished accumulator into FP32
 // running sums with round-to-nearest adds.  Warp 0 lane 0 drives TMA, warp 1 owns the tensor memory and lane 0
 // issues the MMAs, warps 2-3 are idle.
 template <bool SUB>
@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t hh_full[2], hh_empty[2], cr_full[2], cr_empty[2];
+  __shared__ __align__(8) uint64_t hh_empty[NHH], cr_empty;
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -69,12 +69,8 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&hh_full[b], 1);
-      mbar_init(&hh_empty[b], 8);
-      mbar_init(&cr_full[b], 1);
-      mbar_init(&cr_empty[b], 8);
-    }
+    for (int b = 0; b < NHH; ++b) mbar_init(&hh_empty[b], 8);
+    mbar_init(&cr_empty, 8);
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     issued = 0;
@@ -116,13 +112,13 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
     for (; kt < k_tiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
-      const int hb = kt & 1, g = kt / CORR, cb = g & 1;
+      const int hb = kt % NHH, g = kt / CORR;
       const bool g_first = kt % CORR == 0;
-      if (kt >= 2 && !mbar_wait(&hh_empty[hb], (uint32_t)((kt >> 1) - 1) & 1u, &abort_flag)) {
+      if (kt >= NHH && !mbar_wait(&hh_empty[hb], (uint32_t)(kt / NHH - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
-      if (g_first && g >= 2 && !mbar_wait(&cr_empty[cb], (uint32_t)((g >> 1) - 1) & 1u, &abort_flag)) {
+      if (g_first && g >= 1 && !mbar_wait(&cr_empty, (uint32_t)(g - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
@@ -132,19 +128,20 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * STAGE);
-      const uint32_t dh = tmem + (uint32_t)(hb * BN), dc = tmem + (uint32_t)((2 + cb) * BN);
+      const uint32_t dh = tmem + (uint32_t)(hb * BN), dc = tmem + (uint32_t)(NHH * BN);
+      // the hi*hi products of the K-tile first, then its corrections: consecutive instructions share an accumulator
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        umma(dh, sdesc(base + 0 * PLANE + kk * 32), sdesc(base + 2 * PLANE + kk * 32), idesc,
+             kk == 0 ? 0u : 1u);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         const uint32_t ko = kk * 32;
-        const uint64_t ah = sdesc(base + 0 * PLANE + ko), al = sdesc(base + 1 * PLANE + ko);
-        const uint64_t bh = sdesc(base + 2 * PLANE + ko), bl = sdesc(base + 3 * PLANE + ko);
-        umma(dh, ah, bh, idesc, kk > 0 ? 1u : 0u);
-        umma(dc, ah, bl, idesc, (g_first && kk == 0) ? 0u : 1u);
-        umma(dc, al, bh, idesc, 1u);
+        umma(dc, sdesc(base + 0 * PLANE + ko), sdesc(base + 3 * PLANE + ko), idesc, (g_first && kk == 0) ? 0u : 1u);
+        umma(dc, sdesc(base + 1 * PLANE + ko), sdesc(base + 2 * PLANE + ko), idesc, 1u);
       }
       umma_commit(&empty_bar[s]);
-      umma_commit(&hh_full[hb]);
-      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) umma_commit(&cr_full[cb]);
+
     }
     consumed = kt;
     umma_commit(&done_bar);
@@ -156,9 +153,8 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
 #pragma unroll
     for (int j = 0; j < 64; ++j) run[j] = 0.f;
     bool ok = true;
-    // adds accumulator set `set` (0, 1: hi*hi buffers; 2, 3: correction buffers) into the running sums
-    auto drain = [&](uint64_t* full, uint64_t* empty, uint32_t parity, int set) {
-      if (!__all_sync(0xffffffffu, mbar_wait(full, parity, &abort_flag))) return false;
+    // adds accumulator set `set` (0 .. NHH - 1: hi*hi buffers; NHH: the correction buffer) into the running sums
+    auto drain = [&](uint64_t* empty, int set) {
       tc_fence_after();
       tmem_add64(tmem + lane_base + (uint32_t)(set * BN + g * 64), run);
       tc_fence_before();
@@ -167,10 +163,14 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
       return true;
     };
     for (int kt = 0; kt < k_tiles && ok; ++kt) {
-      const int hb = kt & 1, gr = kt / CORR, cb = gr & 1;
-      ok = drain(&hh_full[hb], &hh_empty[hb], (uint32_t)(kt >> 1) & 1u, hb);
-      if (ok && (kt % CORR == CORR - 1 || kt == k_tiles - 1))
-        ok = drain(&cr_full[cb], &cr_empty[cb], (uint32_t)(gr >> 1) & 1u, 2 + cb);
+      // the commit that releases K-tile kt's operand stage arrives once every MMA up to kt has completed, so its
+      // phase also marks the K-tile's accumulators complete; the MMAs of K-tile kt + STAGES, whose commit ends the
+      // stage's next phase, wait for this drain (NHH = STAGES), so the phase cannot pass unobserved
+      const uint32_t parity = (uint32_t)(kt / STAGES) & 1u;
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[kt % STAGES], parity, &abort_flag));
+      if (!ok) break;
+      drain(&hh_empty[kt % NHH], kt % NHH);
+      if (kt % CORR == CORR - 1 || kt == k_tiles - 1) drain(&cr_empty, NHH);
     }
     if (!ok) {
       abort_flag = 1;
