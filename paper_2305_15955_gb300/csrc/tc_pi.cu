@@ -5,16 +5,16 @@
 // The weight is folded into one operand: S = B diag(-w) (per column ia), so that A = I + S B^T.  Each of S and B is
 // split into BF16 planes hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the product is formed from three BF16
 // products hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (the lo*lo term, ~2^-16 relative, is
-// dropped).  On the imaginary axis -w = 4 D / (xi^2 + D^2) > 0 and one real accumulator is used; for complex z
-// the real and imaginary parts of -w give two scaled operands that share the loaded B tile (two accumulators).
+// dropped).  On the imaginary axis -w = 4 D / (xi^2 + D^2) > 0; for complex z the real and imaginary parts of -w
+// give two weighted operands and two launches, which write the real and the imaginary parts of A.
 //
-// Kernel: one CTA per 128 x 128 (real) or 128 x 64 (complex) tile of the lower triangle of A (A is symmetric),
-// 384 threads.  Warp 0 lane 0 drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory
-// stages; warp 1 owns the tensor memory and lane 0 issues tcgen05.mma (M = 128, N = 128 or 64, K = 16 per
-// instruction, both operands K-major); tcgen05.commit releases a stage when the MMAs reading it finish.  The hi*hi
-// products of every K-tile (one buffer per operand stage, in turn) and the corrections of every 32 K-tiles go to
-// fresh accumulators in tensor memory; warps 4-11 read each finished one (tcgen05.ld 32x32b, the accumulator rows they own), add it
-// into FP32 running sums and at the end write A in FP64.  Every wait on an mbarrier is bounded (5 s): on expiry the kernel records
+// Kernel: one CTA per 128 x 128 tile of the lower triangle of A (A is symmetric), 384 threads.  Warp 0 lane 0
+// drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory stages; warp 1 owns the
+// tensor memory and lane 0 issues tcgen05.mma (M = N = 128, K = 16 per instruction, both operands K-major);
+// tcgen05.commit releases a stage when the MMAs reading it finish.  The hi*hi products of every K-tile (one buffer
+// per operand stage, in turn) and the corrections of every 32 K-tiles go to fresh accumulators in tensor memory;
+// warps 4-11 read each finished one (tcgen05.ld 32x32b, the accumulator rows they own), add it into FP32 running
+// sums and at the end write A in FP64.  Every wait on an mbarrier is bounded (5 s): on expiry the kernel records
 // CDWAC_ERR_TIMEOUT, stops issuing, drains what it issued and frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -28,10 +28,10 @@
 namespace {
 using namespace tc;
 
-constexpr int BM = 128, BK = 64;                     // tile rows and K-tile width (tile columns: Cfg::BN)
+constexpr int BM = 128, BK = 64;                     // tile rows and K-tile width
 constexpr int PLANE = BM * BK * 2;                       // bytes of one 128 x 64 BF16 operand tile
 struct Maps {
-  CUtensorMap a0h, a0l, a1h, a1l, bh, bl;
+  CUtensorMap sh, sl, bh, bl;   // planes of the weighted operand S and of B
 };
 
 __device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
@@ -84,32 +84,24 @@ __device__ inline void grouped_tile_coords(int b, int nt, int& ti, int& tj) {
 // the one that frees a K-tile's operand stage also marks its accumulators complete.
 constexpr int CORR = 32;  // K-tiles per correction accumulator (one buffer)
 
-template <int NACC>
-struct Cfg {
-  static constexpr int BN = NACC == 1 ? 128 : 64;          // tile columns: the drain holds NACC x BN = 128 sums
-  static constexpr int B_PLANE = BN * BK * 2;
-  static constexpr int STAGE = 2 * NACC * PLANE + 2 * B_PLANE;
-  static constexpr int STAGES = NACC == 1 ? 3 : 2;
-  static constexpr int SMEM = STAGES * STAGE + 1024;       // + alignment slack
-  static constexpr int ACC_COLS = NACC * BN;               // tensor-memory columns of one accumulator set
-  static constexpr int NHH = STAGES;                       // hi*hi buffers, one per operand stage
-  static constexpr int TMEM_COLS = 4 * ACC_COLS;           // (NHH + 1) x ACC_COLS <= 512 columns
-};
+constexpr int BN = 128;                            // tile columns
+constexpr int STAGE = 4 * PLANE;                   // S hi, S lo, B hi, B lo of one K-tile
+constexpr int STAGES = 3;
+constexpr int SMEM = STAGES * STAGE + 1024;        // + alignment slack
+constexpr int NHH = STAGES;                        // hi*hi accumulator buffers, one per operand stage
+constexpr int TMEM_COLS = (NHH + 1) * BN;          // and the correction accumulator: 512 columns
 
-// A = I + S B^T (lower triangle).  NACC == 1: real A (double*), 128 x 128 tiles.  NACC == 2: complex A (cplx*),
-// re from S0 and im from S1, 128 x 64 tiles (two per 128 x 128 tile of the triangle).
+// A = I + S B^T, lower triangle, written as `part`: -1 the real matrix A (double*), 0 the real parts of a complex
+// matrix (cplx*, with the identity), 1 its imaginary parts (without it); a complex Pi(z) is two launches, one per
+// weight (two 128 x 128 real contractions keep the full-width instructions and the drain's 128 running sums).
 // Warps: 0 = TMA producer (lane 0), 1 = tensor-memory owner and MMA issuer (lane 0), 4..11 = two drain warpgroups
 // (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the tile rows it later writes); 2, 3 idle.
-template <int NACC>
 __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
-                                                         void* A_out, float* negpi32, unsigned* status) {
-  using C = Cfg<NACC>;
-  constexpr int BNC = C::BN;
-  constexpr int NHH = C::NHH;
+                                                         void* A_out, int part, float* negpi32, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[C::STAGES];
-  __shared__ __align__(8) uint64_t empty_bar[C::STAGES];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
   __shared__ __align__(8) uint64_t hh_empty[NHH], cr_empty;
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
@@ -119,11 +111,12 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nt = (n + BM - 1) / BM;
   int ti, tj;
-  grouped_tile_coords(NACC == 1 ? blockIdx.x : blockIdx.x >> 1, nt, ti, tj);
-  const int row0 = ti * BM, col0 = tj * BM + (NACC == 1 ? 0 : (blockIdx.x & 1) * BNC);
-  if (col0 >= n || col0 > row0 + BM - 1) return;   // nothing of the triangle here: the whole CTA leaves at once
+  grouped_tile_coords(blockIdx.x, nt, ti, tj);
+  const int row0 = ti * BM, col0 = tj * BN;
+  if (col0 >= n) return;   // past the triangle: the whole CTA leaves before any barrier or allocation
+
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
@@ -137,7 +130,7 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"((uint32_t)C::TMEM_COLS)
+                 "r"((uint32_t)TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -150,33 +143,29 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
     // ---- TMA producer
     int kt = 0;
     for (; kt < k_tiles; ++kt) {
-      const int s = kt % C::STAGES;
-      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
       if (!mbar_wait(&empty_bar[s], ph ^ 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
-      mbar_expect_tx(&full_bar[s], (uint32_t)C::STAGE);
-      uint8_t* st = smem + s * C::STAGE;
+      mbar_expect_tx(&full_bar[s], (uint32_t)STAGE);
+      uint8_t* st = smem + s * STAGE;
       const int x = kt * BK;
-      tma_load_2d(&maps.a0h, &full_bar[s], st + 0 * PLANE, x, row0);
-      tma_load_2d(&maps.a0l, &full_bar[s], st + 1 * PLANE, x, row0);
-      if (NACC == 2) {
-        tma_load_2d(&maps.a1h, &full_bar[s], st + 2 * PLANE, x, row0);
-        tma_load_2d(&maps.a1l, &full_bar[s], st + 3 * PLANE, x, row0);
-      }
-      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * NACC * PLANE, x, col0);
-      tma_load_2d(&maps.bl, &full_bar[s], st + 2 * NACC * PLANE + C::B_PLANE, x, col0);
+      tma_load_2d(&maps.sh, &full_bar[s], st + 0 * PLANE, x, row0);
+      tma_load_2d(&maps.sl, &full_bar[s], st + 1 * PLANE, x, row0);
+      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * PLANE, x, col0);
+      tma_load_2d(&maps.bl, &full_bar[s], st + 3 * PLANE, x, col0);
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: K-tile kt puts its hi*hi products in hh buffer kt % NHH and its corrections in the
-    // correction buffer (group g = kt / CORR); tensor-memory columns [hh0 | .. | hh(NHH-1) | cr], ACC_COLS each
-    constexpr uint32_t idesc = idesc_bf16(BM, BNC);
+    // correction buffer (group g = kt / CORR); tensor-memory columns [hh0 | hh1 | hh2 | cr], BN each
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
     int kt = 0;
     for (; kt < k_tiles; ++kt) {
-      const int s = kt % C::STAGES;
-      const uint32_t ph = (uint32_t)(kt / C::STAGES) & 1u;
+      const int s = kt % STAGES;
+      const uint32_t ph = (uint32_t)(kt / STAGES) & 1u;
       const int hb = kt % NHH, g = kt / CORR;
       const bool g_first = kt % CORR == 0;
       // the drain must have read a buffer's previous contents before it is overwritten
@@ -193,60 +182,47 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
         break;
       }
       tc_fence_after();
-      const uint32_t base = smem_u32(smem + s * C::STAGE);
+      const uint32_t base = smem_u32(smem + s * STAGE);
+      const uint32_t dh = tmem + (uint32_t)(hb * BN), dc = tmem + (uint32_t)(NHH * BN);
       // the hi*hi products of the K-tile first, then its corrections: consecutive instructions share an accumulator
 #pragma unroll
-      for (int a = 0; a < NACC; ++a) {
-        const uint32_t dh = tmem + (uint32_t)(hb * C::ACC_COLS + a * BNC);
+      for (int kk = 0; kk < BK / 16; ++kk)   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
+        umma(dh, sdesc(base + 0 * PLANE + kk * 32), sdesc(base + 2 * PLANE + kk * 32), idesc, kk == 0 ? 0u : 1u);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t ko = kk * 32;   // 16 BF16 = 32 bytes along K inside the 128-byte swizzle row
-          umma(dh, sdesc(base + (2 * a) * PLANE + ko), sdesc(base + 2 * NACC * PLANE + ko), idesc,
-               kk == 0 ? 0u : 1u);
-        }
-      }
-#pragma unroll
-      for (int a = 0; a < NACC; ++a) {
-        const uint32_t dc = tmem + (uint32_t)(NHH * C::ACC_COLS + a * BNC);
-#pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t ko = kk * 32;
-          const uint64_t bh = sdesc(base + 2 * NACC * PLANE + ko), bl = sdesc(base + 2 * NACC * PLANE + C::B_PLANE + ko);
-          umma(dc, sdesc(base + (2 * a) * PLANE + ko), bl, idesc, (g_first && kk == 0) ? 0u : 1u);
-          umma(dc, sdesc(base + (2 * a + 1) * PLANE + ko), bh, idesc, 1u);
-        }
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t ko = kk * 32;
+        umma(dc, sdesc(base + 0 * PLANE + ko), sdesc(base + 3 * PLANE + ko), idesc, (g_first && kk == 0) ? 0u : 1u);
+        umma(dc, sdesc(base + 1 * PLANE + ko), sdesc(base + 2 * PLANE + ko), idesc, 1u);
       }
       umma_commit(&empty_bar[s]);
-
     }
     consumed = kt;
     umma_commit(&done_bar);   // arrives once every MMA issued above has completed
   } else if (warp >= 4) {
     // ---- drain: two warpgroups; group g (warps 4 + 4g .. 7 + 4g) sums columns [64 g, 64 g + 64) of every
-    // accumulator set (real: tile columns; complex: g = 0 the real, g = 1 the imaginary part) into FP32 running
-    // sums with round-to-nearest adds; warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the tile rows it owns
+    // accumulator into FP32 running sums with round-to-nearest adds; warp w reads tensor-memory lanes
+    // 32 (w % 4) .. + 31, the tile rows it owns
     const int g = (warp - 4) >> 2, q = warp & 3;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    constexpr int HALF = C::ACC_COLS / 2;
+    constexpr int HALF = BN / 2;
     float run[HALF];
 #pragma unroll
     for (int j = 0; j < HALF; ++j) run[j] = 0.f;
     bool ok = true;
-    // adds accumulator set `set` (0 .. NHH - 1: hi*hi buffers; NHH: the correction buffer) into the running sums
+    // adds accumulator `set` (0 .. NHH - 1: hi*hi buffers; NHH: the correction buffer) into the running sums
     auto drain = [&](uint64_t* empty, int set) {
       tc_fence_after();
-      tmem_add64(tmem + lane_base + (uint32_t)(set * C::ACC_COLS + g * HALF), run);
+      tmem_add64(tmem + lane_base + (uint32_t)(set * BN + g * HALF), run);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(empty);
-      return true;
     };
     for (int kt = 0; kt < k_tiles && ok; ++kt) {
       // the commit that releases K-tile kt's operand stage arrives once every MMA up to kt has completed, so its
       // phase also marks the K-tile's accumulators complete; the MMAs of K-tile kt + STAGES, whose commit ends the
       // stage's next phase, wait for this drain (NHH = STAGES), so the phase cannot pass unobserved
-      const uint32_t parity = (uint32_t)(kt / C::STAGES) & 1u;
-      ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[kt % C::STAGES], parity, &abort_flag));
+      const uint32_t parity = (uint32_t)(kt / STAGES) & 1u;
+      ok = __all_sync(0xffffffffu, mbar_wait(&empty_bar[kt % STAGES], parity, &abort_flag));
       if (!ok) break;
       drain(&hh_empty[kt % NHH], kt % NHH);
       if (kt % CORR == CORR - 1 || kt == k_tiles - 1) drain(&cr_empty, NHH);
@@ -254,18 +230,16 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
     if (!ok) abort_flag = 1;
     drain_bar();   // every drain warp is done (a timeout in one ends the others' bounded waits too)
     if (!abort_flag) {
-      // The last accumulator's commit means every MMA has completed and every operand stage has been consumed, so
-      // the operand ring is free: the tile is staged there (row stride ACC_COLS + 1 floats: conflict-free both
-      // ways) and written out as coalesced row segments.
-      constexpr int LDS = C::ACC_COLS + 1;
+      // The last drain means every MMA has completed and every operand stage has been consumed, so the operand
+      // ring is free: the tile is staged there (row stride BN + 1 floats: conflict-free both ways) and written
+      // out as coalesced row segments, this warp's 32 rows and its group's 64 columns.
+      constexpr int LDS = BN + 1;
       float* stg = reinterpret_cast<float*>(smem);
 #pragma unroll
       for (int j = 0; j < HALF; ++j) stg[(q * 32 + lane) * LDS + g * HALF + j] = run[j];
       drain_bar();
-      // real: this warp's 32 rows, columns [64 g, 64 g + 64); complex: 16 of its rows, all 64 columns
-      const int r_lo = NACC == 1 ? 0 : 16 * g, r_hi = NACC == 1 ? 32 : 16 * g + 16;
-      const int c_lo = NACC == 1 ? g * HALF : 0;
-      for (int rr = r_lo; rr < r_hi; ++rr) {
+      const int c_lo = g * HALF;
+      for (int rr = 0; rr < 32; ++rr) {
         const int row = row0 + q * 32 + rr;
         if (row >= n) break;
         const float* src = stg + (q * 32 + rr) * LDS;
@@ -273,15 +247,16 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
           const int col = col0 + j;
           if (col > row || col >= n) continue;
           const double diag = col == row ? 1.0 : 0.0;
-          if constexpr (NACC == 1) {
+          if (part < 0) {
             reinterpret_cast<double*>(A_out)[(long)row * n + col] = diag + (double)src[j];
             if (negpi32) negpi32[(long)row * n + col] = src[j];   // -Pi in FP32 for the Pi O product
           } else {
-            reinterpret_cast<cplx*>(A_out)[(long)row * n + col] = mkc(diag + (double)src[j], (double)src[BNC + j]);
+            double* Ac = reinterpret_cast<double*>(A_out) + 2 * ((long)row * n + col) + part;
+            *Ac = (part == 0 ? diag : 0.0) + (double)src[j];
           }
         }
       }
-      if (NACC == 1 && negpi32) {
+      if (part < 0 && negpi32) {
         // the transposed (upper) entries: the 32 lanes hold consecutive rows, so every store is coalesced
         const int row = row0 + q * 32 + lane;
         for (int j = c_lo; j < c_lo + HALF; ++j) {
@@ -302,14 +277,14 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
       raise_status(status, DEV_ERR_TIMEOUT);
       // drain loads that were issued but never consumed, so no copy lands after the CTA exits
       for (int kt = consumed; kt < issued; ++kt)
-        mbar_wait(&full_bar[kt % C::STAGES], (uint32_t)(kt / C::STAGES) & 1u, nullptr);
+        mbar_wait(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, nullptr);
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TMEM_COLS)
                  : "memory");
   }
 }
@@ -449,19 +424,17 @@ int elementwise_blocks(cdwac_ctx* ctx, long work) {
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
-template <int NACC>
-cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, int n, void* A, float* negpi32, cudaStream_t st) {
-  using C = Cfg<NACC>;
+// One launch of the contraction with the weighted planes (sh, sl): part as in tc_syrk_kernel.
+cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl, int n,
+                      void* A, int part, float* negpi32, cudaStream_t st) {
   Maps maps;
   memset(&maps, 0, sizeof(maps));
-  bool ok = make_map(&maps.a0h, s.s0h, n, s.kpad) && make_map(&maps.a0l, s.s0l, n, s.kpad) &&
-            make_map(&maps.bh, s.bh, n, s.kpad, C::BN) && make_map(&maps.bl, s.bl, n, s.kpad, C::BN);
-  if (NACC == 2) ok = ok && make_map(&maps.a1h, s.s1h, n, s.kpad) && make_map(&maps.a1l, s.s1l, n, s.kpad);
-  if (!ok) return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
-  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel<NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM));
+  if (!make_map(&maps.sh, sh, n, s.kpad) || !make_map(&maps.sl, sl, n, s.kpad) || !make_map(&maps.bh, s.bh, n, s.kpad) ||
+      !make_map(&maps.bl, s.bl, n, s.kpad))
+    return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
   const int nt = (n + BM - 1) / BM;
-  const int tiles = nt * (nt + 1) / 2 * (BM / C::BN);     // complex: two 128 x 64 halves per triangle tile
-  tc_syrk_kernel<NACC><<<tiles, 384, C::SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, negpi32, ctx->d_status);
+  tc_syrk_kernel<<<nt * (nt + 1) / 2, 384, SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, part, negpi32, ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }
@@ -533,7 +506,7 @@ cdwac_status tc_pi_imag(cdwac_ctx* ctx, const void* shared, void* lane, const vo
   }
   if (rc) return rc;
   ProfScope ps(ctx, PROF_PI_TC_IMAG, st);
-  return run_syrk<1>(ctx, s, n_aux, A, negpi32, st);
+  return run_syrk(ctx, s, s.s0h, s.s0l, n_aux, A, -1, negpi32, st);
 }
 
 cdwac_status tc_pi_complex(cdwac_ctx* ctx, const void* shared, void* lane, const void* O_ia, int dtype,
@@ -546,5 +519,7 @@ cdwac_status tc_pi_complex(cdwac_ctx* ctx, const void* shared, void* lane, const
   }
   if (rc) return rc;
   ProfScope ps(ctx, PROF_PI_TC_CPLX, st);
-  return run_syrk<2>(ctx, s, n_aux, A, nullptr, st);
+  // real and imaginary parts as two real contractions sharing the B planes
+  if ((rc = run_syrk(ctx, s, s.s0h, s.s0l, n_aux, A, 0, nullptr, st))) return rc;
+  return run_syrk(ctx, s, s.s1h, s.s1l, n_aux, A, 1, nullptr, st);
 }
