@@ -15,23 +15,25 @@
 //     its own FP32 tensor-memory accumulator.  All partial sums of one level are integers of magnitude below
 //     64 x 147 456 < 2^24 (real, largest level) or 128 x 40 960 < 2^23 (complex, K = 128), so every
 //     accumulation is exact.
-//   * the epilogue forms sum_L 2^-BL acc_L exactly in 64-bit integers (GB300's FP64 units are the scarce
-//     resource), converts it once to FP64, scales it by 2^(e_i + e_j) with an integer add to the exponent field
-//     and subtracts it from A.
+//   * the epilogue forms sum_L 2^-BL acc_L exactly in 64-bit integers, rounds it once to FP64 scaled by
+//     2^(e_i + e_j) (both with integer instructions: GB300's FP64 units are the scarce resource) and subtracts it
+//     from A, the one FP64 instruction per element.
 //
 // The digits dropped (levels above S + 1 and the remainders r) are below about 2^-54 max|W_i| max|L_j| per
 // column, the size of the rounding error of an FP64 dot product of this length.
 //
-// Complex symmetric A (no conjugation): Re -= Wr Lr - Wi Li, Im -= Wr Li + Wi Lr.  The CTA loads the digits of
-// Wr with those of Lr and Li, issues Re += Wr Lr and Im += Wr Li, then reloads the operand buffer with the digits
-// of Wi and issues Re += -(Wi Li) (negated-A instruction descriptor) and Im += Wi Lr.
+// Complex symmetric A (no conjugation): Re -= Wr Lr - Wi Li, Im -= Wr Li + Wi Lr.  Two CTAs share a complex
+// tile, one per part of A: the re CTA issues Re += Wr Lr and then Re += -(Wi Li) (negated-A instruction
+// descriptor), the im CTA Im += Wr Li and then Im += Wi Lr.
 //
-// One CTA per 128 x BN tile of the trailing lower triangle (BN = 64 real, 32 complex): one elected thread issues
-// TMA (3-D maps over the digit planes, 128-byte swizzle), one issues the MMAs, all warps drain tensor memory
-// (tcgen05.ld 32x32b; eight warps, two per lane quarter), stage the FP64 result in shared memory and update A with
-// coalesced row segments.  Every
-// mbarrier wait is bounded; on expiry the kernel records CDWAC_ERR_TIMEOUT, waits for the copies it issued and
-// frees its tensor memory.
+// One CTA per 128 x 32 tile of the trailing lower triangle (per part, complex), 256 threads, two CTAs per SM
+// (93-97 KB of shared memory and 256 tensor-memory columns each), so that one CTA's epilogue overlaps the other's
+// loads and MMAs: one elected thread issues TMA (3-D maps over the digit planes, 128-byte swizzle; the tile's L
+// digits stay resident, the W digits stream through a ring), one issues the MMAs, all eight warps drain tensor
+// memory (tcgen05.ld 32x32b; two warps per lane quarter), recombine the levels in 64-bit integers, assemble the
+// FP64 update with integer instructions, stage it in shared memory and update A with coalesced row segments.
+// Every mbarrier wait is bounded; on expiry the kernel records CDWAC_ERR_TIMEOUT, waits for the copies it issued
+// and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <string.h>
@@ -55,15 +57,16 @@ struct OzCfg {
   // complex 8 x 7 bits (its level sums run over K = 128 products and must stay below 2^24 as well)
   static constexpr int S = CPLX ? 8 : 7;
   static constexpr int BETA = CPLX ? 7 : 8;
-  static constexpr int NPART = CPLX ? 2 : 1;
-  static constexpr int BN = CPLX ? 32 : 64;
+  static constexpr int NPART = CPLX ? 2 : 1;        // parts (re, im) of W and of L
+  static constexpr int BN = 32;                     // tile columns
   static constexpr int A_TILE = BM * ROWB;          // one digit of 128 W rows (16 KB)
-  static constexpr int B_TILE = BN * ROWB;          // one digit of BN L rows
-  static constexpr int A_BYTES = S * A_TILE;        // the digits of one part of W
-  static constexpr int B_BYTES = NPART * S * B_TILE;
-  static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
-  static constexpr int TMEM_COLS = 512;             // 7 levels x 64 columns, or (re, im) x 8 levels x 32 columns
-  static constexpr int IM_COL = 256;                // first tensor-memory column of the imaginary accumulators
+  static constexpr int B_TILE = BN * ROWB;          // one digit of 32 L rows (4 KB)
+  static constexpr int B_BYTES = NPART * S * B_TILE;   // every digit of every part of L: 28 KB real, 64 KB complex
+  static constexpr int NS = CPLX ? 2 : 4;           // stages of the W-digit ring
+  static constexpr int WLOADS = NPART * S;          // W digit planes per tile: Wr digits, then (complex) Wi digits
+  // 93 KB (real) or 97 KB (complex) of dynamic shared memory: two CTAs per SM
+  static constexpr int SMEM = B_BYTES + NS * A_TILE + 1024;
+  static constexpr int TMEM_COLS = 256;             // S levels x 32 columns (224 real, 256 complex): two CTAs per SM
   // recombination scale 2^SHIFT: the level-2 sum (|acc_2| <= K d_1^2 = 64 * 2^16 real, 128 * 2^14 complex) times
   // 2^(SHIFT - 2 BETA) stays below 2^63, so the int64 sum of all levels cannot overflow
   static constexpr int SHIFT = CPLX ? 55 : 56;
@@ -73,24 +76,40 @@ struct OzMaps {
   CUtensorMap w, l;
 };
 
-// RN(a) 2^k as an FP64 number: the hardware conversion of a (round to nearest), then the power of two applied to
-// the exponent field with an integer add instead of an FP64 multiply (GB300 issues an FP64 warp instruction in about
-// 64 cycles).  Exact as long as the result stays in the normal range, which these updates do.
+// RN(a) 2^k as an FP64 number, assembled with integer instructions (GB300 issues an FP64 warp instruction, the
+// conversion included, in about 64 cycles, an integer one in one or two): the magnitude is normalised with a
+// count of leading zeros, its top 53 bits are rounded to nearest (ties to even) on the 11 bits below them, and
+// the biased exponent 1086 - lz + k is added above the mantissa (a carry out of the rounding moves into the
+// exponent field, as it should).  Results outside the normal range take the FP64 path (not reached by these
+// updates).
 __device__ inline double scaled_int64(long long a, int k) {
-  const long long b = __double_as_longlong(__ll2double_rn(a));
-  return __longlong_as_double((b & 0x7FF0000000000000ll) ? b + ((long long)k << 52) : b);
+  if (a == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)a & 0x8000000000000000ull;
+  unsigned long long m = a < 0 ? 0ull - (unsigned long long)a : (unsigned long long)a;
+  const int lz = __clzll((long long)m);
+  const int E = 1086 - lz + k;
+  if (E < 2 || E > 2045) return ldexp((double)a, k);
+  m <<= lz;
+  const unsigned rem = (unsigned)(m & 0x7FFull);
+  m >>= 11;
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  return __longlong_as_double((long long)(sgn | (((unsigned long long)(E - 1) << 52) + m)));
 }
 
+// One CTA per 128 x 32 tile of the trailing lower triangle (complex: two CTAs per tile, one per part of A), two
+// CTAs per SM, so that one CTA's epilogue (tensor-memory drain, integer recombination, read-modify-write of A)
+// overlaps the other's loads and MMAs.  The L digits of the tile stay in shared memory; the W digits stream
+// through a ring of NS stages (the MMAs of W digit s pair it with L digits t <= S - 1 - s).
 template <bool CPLX>
-__global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
+__global__ void __launch_bounds__(256, 2) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
                                                            int k1, const int* __restrict__ ew,
                                                            const int* __restrict__ el, int part, unsigned* status) {
   using C = OzCfg<CPLX>;
-  constexpr int S = C::S, BETA = C::BETA;
-  constexpr int BN = C::BN;
+  constexpr int S = C::S, BETA = C::BETA, BN = C::BN, NS = C::NS;
   constexpr int Q = K / BN;     // column tiles in the next 64-column block
   constexpr int CT = BM / BN;   // column tiles per 128 rows
-  int b = blockIdx.x, ti = 0;
+  int b = CPLX ? (int)(blockIdx.x >> 1) : (int)blockIdx.x, ti = 0;
+  const int pr = CPLX ? (int)(blockIdx.x & 1) : 0;   // part of A this CTA updates: 0 = re, 1 = im
   for (; ti < (1 << 20); ++ti) {
     const int cnt = part == 1 ? Q : (part == 0 ? CT * (ti + 1) : CT * (ti + 1) - Q);
     if (b < cnt) break;
@@ -102,22 +121,26 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
 
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + C::A_BYTES;
-  __shared__ __align__(8) uint64_t bar_a0, bar_a1, bar_mma0, bar_done;
+  uint8_t* sB = smem;                  // L digits: plane p S + t at p S + t
+  uint8_t* sA = smem + C::B_BYTES;     // W-digit ring
+  __shared__ __align__(8) uint64_t bar_l, full_bar[NS], empty_bar[NS], bar_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
-  __shared__ int loads_issued;
+  __shared__ int l_issued, w_issued, w_consumed;
   __shared__ int exp_w[BM], exp_l[BN];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
   if (threadIdx.x == 0) {
-    mbar_init(&bar_a0, 1);
-    mbar_init(&bar_a1, 1);
-    mbar_init(&bar_mma0, 1);
+    mbar_init(&bar_l, 1);
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
     mbar_init(&bar_done, 1);
     abort_flag = 0;
-    loads_issued = 0;
+    l_issued = 0;
+    w_issued = 0;
+    w_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int r = threadIdx.x; r < BM; r += blockDim.x) exp_w[r] = row0 + r < n ? ew[row0 + r] : 0;
@@ -134,57 +157,53 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
   const uint32_t tmem = tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---- TMA producer: digits of W (part 0) and of every part of L; for complex A then the digits of Wi
-    mbar_expect_tx(&bar_a0, (uint32_t)(C::A_BYTES + C::B_BYTES));
-    for (int s = 0; s < S; ++s) tma_load_3d(&maps.w, &bar_a0, sA + s * C::A_TILE, 0, row0, s);
+    // ---- TMA producer: every digit of every part of L, then the W digit planes q = 0 .. WLOADS - 1 (Wr digits,
+    // then Wi digits) through the ring
+    mbar_expect_tx(&bar_l, (uint32_t)C::B_BYTES);
     for (int p = 0; p < C::NPART; ++p)
-      for (int s = 0; s < S; ++s) tma_load_3d(&maps.l, &bar_a0, sB + (p * S + s) * C::B_TILE, 0, col0, p * S + s);
-    loads_issued = 1;
-    if (CPLX) {
-      if (mbar_wait(&bar_mma0, 0, &abort_flag)) {   // the phase-0 MMAs have finished reading sA
-        mbar_expect_tx(&bar_a1, (uint32_t)C::A_BYTES);
-        for (int s = 0; s < S; ++s) tma_load_3d(&maps.w, &bar_a1, sA + s * C::A_TILE, 0, row0, S + s);
-        loads_issued = 3;
-      } else {
+      for (int s = 0; s < S; ++s) tma_load_3d(&maps.l, &bar_l, sB + (p * S + s) * C::B_TILE, 0, col0, p * S + s);
+    l_issued = 1;
+    int q = 0;
+    for (; q < C::WLOADS; ++q) {
+      const int st = q % NS;
+      if (q >= NS && !mbar_wait(&empty_bar[st], (uint32_t)(q / NS - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
+        break;
       }
+      mbar_expect_tx(&full_bar[st], (uint32_t)C::A_TILE);
+      tma_load_3d(&maps.w, &full_bar[st], sA + st * C::A_TILE, 0, row0, q);
     }
+    w_issued = q;
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: level idx = s + t (0-based digits) accumulates in columns idx * BN (+ IM_COL)
+    // ---- MMA issuer: W digit s (part ph) times L digit t of the paired part accumulates in level s + t, columns
+    // (s + t) BN.  Real: W L.  Complex, re CTA: Wr Lr - Wi Li (negated-A descriptor); im CTA: Wr Li + Wi Lr.
     constexpr uint32_t id = idesc_bf16(BM, BN);
-    bool ok = mbar_wait(&bar_a0, 0, &abort_flag);
+    bool ok = mbar_wait(&bar_l, 0, &abort_flag);
+    int q = 0;
     if (ok) {
-      tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      for (int s = 0; s < S; ++s)
+      for (; q < C::WLOADS; ++q) {
+        const int st = q % NS;
+        if (!mbar_wait(&full_bar[st], (uint32_t)(q / NS) & 1u, &abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const int ph = q / S, s = q % S;
+        const int lp = CPLX ? (ph ^ pr) : 0;
+        const uint32_t neg = (CPLX && ph == 1 && pr == 0) ? NEG_A : 0u;
+        const uint32_t abase = a0 + st * C::A_TILE;
         for (int t = 0; s + t < S; ++t) {
           const uint32_t d = tmem + (uint32_t)((s + t) * BN);
+          const uint32_t bbase = b0 + (lp * S + t) * C::B_TILE;
 #pragma unroll
-          for (int kk = 0; kk < K / 16; ++kk) {
-            const uint32_t acc = (s > 0 || kk > 0) ? 1u : 0u;   // digit 0 is the first to reach every level
-            const uint64_t ad = sdesc(a0 + s * C::A_TILE + kk * 32);
-            umma(d, ad, sdesc(b0 + t * C::B_TILE + kk * 32), id, acc);
-            if (CPLX) umma(d + C::IM_COL, ad, sdesc(b0 + (S + t) * C::B_TILE + kk * 32), id, acc);
-          }
+          for (int kk = 0; kk < K / 16; ++kk)   // q = 0 (digit 0 of Wr) is the first to reach every level
+            umma(d, sdesc(abase + kk * 32), sdesc(bbase + kk * 32), id | neg, (q > 0 || kk > 0) ? 1u : 0u);
         }
-      umma_commit(&bar_mma0);
-      if (CPLX) {
-        ok = mbar_wait(&bar_a1, 0, &abort_flag);
-        if (ok) {
-          tc_fence_after();
-          for (int s = 0; s < S; ++s)
-            for (int t = 0; s + t < S; ++t) {
-              const uint32_t d = tmem + (uint32_t)((s + t) * BN);
-#pragma unroll
-              for (int kk = 0; kk < K / 16; ++kk) {
-                const uint64_t ad = sdesc(a0 + s * C::A_TILE + kk * 32);
-                umma(d, ad, sdesc(b0 + (S + t) * C::B_TILE + kk * 32), id | NEG_A, 1u);   // Re += -(Wi Li)
-                umma(d + C::IM_COL, ad, sdesc(b0 + t * C::B_TILE + kk * 32), id, 1u);     // Im += Wi Lr
-              }
-            }
-        }
+        umma_commit(&empty_bar[st]);   // the stage is free once these MMAs have read it
       }
     }
+    w_consumed = q;
     if (!ok) abort_flag = 1;
     umma_commit(&bar_done);   // arrives once every MMA issued above has completed
   }
@@ -196,85 +215,61 @@ __global__ void __launch_bounds__(256, 1) oz_update_kernel(const __grid_constant
   const bool good = __syncthreads_and(done_ok ? 1 : 0) && !abort_flag;
   if (threadIdx.x == 0 && !good) {
     raise_status(status, DEV_ERR_TIMEOUT);
-    if (loads_issued & 1) mbar_wait(&bar_a0, 0, nullptr);   // no copy may land after the CTA exits
-    if (loads_issued & 2) mbar_wait(&bar_a1, 0, nullptr);
+    // no copy may land after the CTA exits: wait for the L digits and for every W load not consumed
+    if (l_issued) mbar_wait(&bar_l, 0, nullptr);
+    for (int q = w_consumed; q < w_issued; ++q) mbar_wait(&full_bar[q % NS], (uint32_t)(q / NS) & 1u, nullptr);
   }
   if (good) {
-    // Every MMA has completed, so the operand buffers are free for staging: slot [unit][quarter][32 rows][33].
-    // Warp w reads tensor-memory lanes 32 (w % 4) .. + 31, i.e. tile rows of quarter q = w % 4; the two warpgroups
-    // g = w / 4 take one unit each: column chunk g (real, 64 columns) or part g = re, im (complex, 32 columns).
-    // In the read-modify-write lane = column, so each row segment is one coalesced access; the A values are
-    // fetched before the tensor-memory drain so that their latency hides behind the integer recombination.
-    using T = typename std::conditional<CPLX, cplx, double>::type;
-    T* Ab = reinterpret_cast<T*>(A_out);
+    // Every MMA has completed, so the operand buffers are free for staging the update, [128 rows][33].
+    // Drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and columns 16 (w / 4) .. + 15.
+    // Read-modify-write: warp w updates tile rows 16 w .. 16 w + 15, lane = column, one coalesced row segment
+    // each (the other CTA on the SM hides the latency of its loads).
+    double* Ad = reinterpret_cast<double*>(A_out);
+    constexpr long ES = CPLX ? 2 : 1;   // doubles per element of A
     double* stage = reinterpret_cast<double*>(smem);
-    const int wq = warp & 3, wg = warp >> 2;
+    const int wq = warp & 3, h = warp >> 2;
     const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-    const int c0 = CPLX ? 0 : 32 * wg;                 // column chunk of this warpgroup
-    const int pp = CPLX ? wg : 0;                      // part drained by this warpgroup
-    const int rbase = row0 + wq * 32 + (CPLX ? 16 * wg : 0);   // first row written by this warp
-    const int col = col0 + c0 + lane;
-    T cv0[16], cv1[16];
-#pragma unroll
-    for (int rr = 0; rr < 16; ++rr) {
-      const int row = rbase + rr;
-      if (row < n && col <= row) cv0[rr] = Ab[(long)row * n + col];
-    }
+    const int col = col0 + lane;
     {
-      // exact integer recombination N = sum_L acc_L 2^(SH - 7L) on the integer pipe (bits of the lowest levels
-      // below 2^-SH are rounded off, < 2^-60 of the largest term)
-      long long acc[32];
+      // exact integer recombination N = sum_L acc_L 2^(SHIFT - BETA (L + 2)) on the integer pipe (bits of the
+      // lowest levels below 2^-SHIFT are rounded off, < 2^-60 of the largest term)
+      long long acc[16];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0;
-#pragma unroll 1
-      for (int idx = 0; idx < S; ++idx) {
-        uint32_t v[32];
-        tmem_ld32(tmem + lane_base + (uint32_t)(pp * C::IM_COL + idx * BN + c0), v);
-        constexpr int SH = C::SHIFT;
-        const int sh = SH - BETA * (idx + 2);
+      for (int j = 0; j < 16; ++j) acc[j] = 0;
+      auto add_level = [&](const uint32_t(&v)[16], int L) {
+        const int sh = C::SHIFT - BETA * (L + 2);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact: an integer < 2^23
+        for (int j = 0; j < 16; ++j) {
+          const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact: an integer < 2^24
           acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> -sh);   // rounded, not floored
         }
+      };
+#pragma unroll 1
+      for (int L = 0; L < S; L += 2) {
+        uint32_t v0[16], v1[16];
+        tmem_ld16_async(tmem + lane_base + (uint32_t)(L * BN + 16 * h), v0);
+        if (L + 1 < S) tmem_ld16_async(tmem + lane_base + (uint32_t)((L + 1) * BN + 16 * h), v1);
+        tmem_wait_ld16(v0, v1);
+        add_level(v0, L);
+        if (L + 1 < S) add_level(v1, L + 1);
       }
-      // staged: the scaled update N 2^(e_row + e_col - SHIFT) of element (tile row wq * 32 + lane, column c0 + j);
-      // the read-modify-write below is then one FP64 subtraction per element
-      double* st = stage + ((wg * 4 + wq) * 32) * 33;
+      // staged: the scaled update N 2^(e_row + e_col - SHIFT) of element (tile row wq * 32 + lane, column 16 h + j)
+      double* st = stage + (wq * 32 + lane) * 33 + 16 * h;
       const int kr = exp_w[wq * 32 + lane] - C::SHIFT;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) st[lane * 33 + j] = scaled_int64(acc[j], kr + exp_l[c0 + j]);
+      for (int j = 0; j < 16; ++j) st[j] = scaled_int64(acc[j], kr + exp_l[16 * h + j]);
     }
-    if (CPLX)
-      __syncthreads();   // both parts of every row staged
-    else
-      __syncwarp();
-    if (!CPLX) {
+    __syncthreads();
+    double cv[16];
 #pragma unroll
-      for (int rr = 0; rr < 16; ++rr) {
-        const int row = rbase + 16 + rr;
-        if (row < n && col <= row) cv1[rr] = Ab[(long)row * n + col];
-      }
+    for (int r = 0; r < 16; ++r) {
+      const int row = row0 + 16 * warp + r;
+      cv[r] = (row < n && col <= row) ? Ad[((long)row * n + col) * ES + pr] : 0.0;
     }
-    const double* st0 = stage + ((CPLX ? 0 : wg) * 4 + wq) * 32 * 33;
-    const double* st1 = stage + (4 + wq) * 32 * 33;
-    const int r_off = CPLX ? 16 * wg : 0;              // first staged row of this warp within its quarter
 #pragma unroll
-    for (int h = 0; h < (CPLX ? 1 : 2); ++h) {
-#pragma unroll
-      for (int rr = 0; rr < 16; ++rr) {
-        const int r = r_off + h * 16 + rr, row = row0 + wq * 32 + r;
-        if (row < n && col <= row) {
-          T v = h == 0 ? cv0[rr] : cv1[rr];
-          if constexpr (!CPLX) {
-            v = v - st0[r * 33 + lane];
-          } else {
-            v.x = v.x - st0[r * 33 + lane];
-            v.y = v.y - st1[r * 33 + lane];
-          }
-          Ab[(long)row * n + col] = v;
-        }
-      }
+    for (int r = 0; r < 16; ++r) {
+      const int row = row0 + 16 * warp + r;
+      if (row < n && col <= row) Ad[((long)row * n + col) * ES + pr] = cv[r] - stage[(16 * warp + r) * 33 + lane];
     }
   }
   tc_fence_before();
@@ -438,13 +433,16 @@ cdwac_status ozaki_update(cdwac_ctx* ctx, const OzakiPlan& plan, int buf, T* A, 
   if (rows <= 0) return CDWAC_OK;
   const long mb = (rows + BM - 1) / BM, ct = BM / C::BN, q = K / C::BN;
   const long all = ct * mb * (mb + 1) / 2;
-  const long grid = part == 0 ? all : (part == 1 ? q * mb : all - q * mb);
-  if (grid <= 0) return CDWAC_OK;
+  const long tiles = part == 0 ? all : (part == 1 ? q * mb : all - q * mb);
+  if (tiles <= 0) return CDWAC_OK;
+  const long grid = tiles * C::NPART;   // complex: one CTA per part of A
   OzMaps maps;
   maps.w = plan.wmap[buf];
   maps.l = plan.lmap[buf];
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(oz_update_kernel<CPLX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            C::SMEM));
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(oz_update_kernel<CPLX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                           (int)cudaSharedmemCarveoutMaxShared));
   oz_update_kernel<CPLX><<<(unsigned)grid, 256, C::SMEM, st>>>(maps, A, n, k1, plan.ew[buf], plan.el[buf], part,
                                                               ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
