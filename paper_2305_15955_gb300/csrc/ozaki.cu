@@ -38,6 +38,7 @@
 #include <cuda_bf16.h>
 #include <string.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "ozaki.cuh"
@@ -59,14 +60,16 @@ struct OzCfg {
   static constexpr int BETA = CPLX ? 7 : 8;
   static constexpr int NPART = CPLX ? 2 : 1;        // parts (re, im) of W and of L
   static constexpr int BN = 32;                     // tile columns
+  static constexpr int NT = 256;                    // threads: eight warps, two per tensor-memory lane quarter
   static constexpr int A_TILE = BM * ROWB;          // one digit of 128 W rows (16 KB)
   static constexpr int B_TILE = BN * ROWB;          // one digit of 32 L rows (4 KB)
   static constexpr int B_BYTES = NPART * S * B_TILE;   // every digit of every part of L: 28 KB real, 64 KB complex
-  static constexpr int NS = CPLX ? 2 : 4;           // stages of the W-digit ring
+  static constexpr int NS = 2;                      // stages of the W-digit ring
   static constexpr int WLOADS = NPART * S;          // W digit planes per tile: Wr digits, then (complex) Wi digits
-  // 93 KB (real) or 97 KB (complex) of dynamic shared memory: two CTAs per SM
+  // 61 KB (real) or 97 KB (complex) of dynamic shared memory: two CTAs per SM
   static constexpr int SMEM = B_BYTES + NS * A_TILE + 1024;
-  static constexpr int TMEM_COLS = 256;             // S levels x 32 columns (224 real, 256 complex): two CTAs per SM
+  static constexpr int MIN_CTAS = 2;
+  static constexpr int TMEM_COLS = 256;             // S levels x 32 columns (224 real, 256 complex)
   // recombination scale 2^SHIFT: the level-2 sum (|acc_2| <= K d_1^2 = 64 * 2^16 real, 128 * 2^14 complex) times
   // 2^(SHIFT - 2 BETA) stays below 2^63, so the int64 sum of all levels cannot overflow
   static constexpr int SHIFT = CPLX ? 55 : 56;
@@ -101,7 +104,7 @@ __device__ inline double scaled_int64(long long a, int k) {
 // overlaps the other's loads and MMAs.  The L digits of the tile stay in shared memory; the W digits stream
 // through a ring of NS stages (the MMAs of W digit s pair it with L digits t <= S - 1 - s).
 template <bool CPLX>
-__global__ void __launch_bounds__(256, 2) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
+__global__ void __launch_bounds__(OzCfg<CPLX>::NT, OzCfg<CPLX>::MIN_CTAS) oz_update_kernel(const __grid_constant__ OzMaps maps, void* A_out, int n,
                                                            int k1, const int* __restrict__ ew,
                                                            const int* __restrict__ el, int part, unsigned* status) {
   using C = OzCfg<CPLX>;
@@ -220,16 +223,17 @@ __global__ void __launch_bounds__(256, 2) oz_update_kernel(const __grid_constant
     for (int q = w_consumed; q < w_issued; ++q) mbar_wait(&full_bar[q % NS], (uint32_t)(q / NS) & 1u, nullptr);
   }
   if (good) {
-    // Every MMA has completed, so the operand buffers are free for staging the update, [128 rows][33].
-    // Drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and columns 16 (w / 4) .. + 15.
-    // Read-modify-write: warp w updates tile rows 16 w .. 16 w + 15, lane = column, one coalesced row segment
-    // each (the other CTA on the SM hides the latency of its loads).
+    // Every MMA has completed, so the operand buffers are free for staging the update, [128 rows][BN + 1].
+    // Drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and 16 columns, 16 (w / 4) .. + 15.
+    // Read-modify-write: warp w updates tile rows RW w .. RW w + RW - 1, 32 / BN rows per instruction with lane =
+    // (row, column), coalesced row segments (the other CTAs on the SM hide the latency of its loads).
+    constexpr int NW = C::NT / 32, SLD = BN + 1, RW = BM / NW, RPP = 32 / BN;
+    static_assert(BN / (NW / 4) == 16, "sixteen accumulator columns per thread");
     double* Ad = reinterpret_cast<double*>(A_out);
     constexpr long ES = CPLX ? 2 : 1;   // doubles per element of A
     double* stage = reinterpret_cast<double*>(smem);
     const int wq = warp & 3, h = warp >> 2;
     const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
-    const int col = col0 + lane;
     {
       // exact integer recombination N = sum_L acc_L 2^(SHIFT - BETA (L + 2)) on the integer pipe (bits of the
       // lowest levels below 2^-SHIFT are rounded off, < 2^-60 of the largest term)
@@ -254,22 +258,23 @@ __global__ void __launch_bounds__(256, 2) oz_update_kernel(const __grid_constant
         if (L + 1 < S) add_level(v1, L + 1);
       }
       // staged: the scaled update N 2^(e_row + e_col - SHIFT) of element (tile row wq * 32 + lane, column 16 h + j)
-      double* st = stage + (wq * 32 + lane) * 33 + 16 * h;
+      double* st = stage + (wq * 32 + lane) * SLD + 16 * h;
       const int kr = exp_w[wq * 32 + lane] - C::SHIFT;
 #pragma unroll
       for (int j = 0; j < 16; ++j) st[j] = scaled_int64(acc[j], kr + exp_l[16 * h + j]);
     }
     __syncthreads();
-    double cv[16];
+    const int rsub = lane / BN, col = col0 + lane % BN;
+    double cv[RW / RPP];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int row = row0 + 16 * warp + r;
-      cv[r] = (row < n && col <= row) ? Ad[((long)row * n + col) * ES + pr] : 0.0;
+    for (int p = 0; p < RW / RPP; ++p) {
+      const int row = row0 + RW * warp + RPP * p + rsub;
+      cv[p] = (row < n && col <= row) ? Ad[((long)row * n + col) * ES + pr] : 0.0;
     }
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      const int row = row0 + 16 * warp + r;
-      if (row < n && col <= row) Ad[((long)row * n + col) * ES + pr] = cv[r] - stage[(16 * warp + r) * 33 + lane];
+    for (int p = 0; p < RW / RPP; ++p) {
+      const int r = RW * warp + RPP * p + rsub, row = row0 + r;
+      if (row < n && col <= row) Ad[((long)row * n + col) * ES + pr] = cv[p] - stage[r * SLD + lane % BN];
     }
   }
   tc_fence_before();
@@ -278,6 +283,232 @@ __global__ void __launch_bounds__(256, 2) oz_update_kernel(const __grid_constant
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)C::TMEM_COLS)
                  : "memory");
+  }
+}
+
+// ---- real trailing update by row strips -----------------------------------------------------------------------
+// One CTA per chunk of up to `chunk` consecutive 128 x 32 tiles of one 128-row strip (real A).  The strip's seven
+// W digit planes (112 KB) are loaded once and stay in shared memory; the L digits of successive tiles (28 KB each)
+// and their tensor-memory accumulators (7 levels x 32 columns) are double-buffered, so the MMAs of tile j + 1 run
+// while the epilogue warps drain, recombine and write tile j.  640 threads: warp 0 issues TMA, warp 1 the MMAs,
+// warps 4-19 form the epilogue (they stage the FP64 update in shared memory and update A with coalesced row
+// segments).
+constexpr int SBN = 32;                            // tile columns
+constexpr int SS = 7, SBETA = 8, SSHIFT = 56;      // real digits (as OzCfg<false>)
+constexpr int S_WB = SS * BM * ROWB;               // the strip's W digits: 112 KB
+constexpr int S_LB = SS * SBN * ROWB;              // one tile's L digits: 28 KB
+constexpr int S_SLD = 9;                           // staging row stride (doubles): 8 columns + 1
+constexpr int S_STG = 16 * 32 * S_SLD * 8;         // a 32 x 8 slot per epilogue warp: 36 KB
+constexpr int S_SMEM = S_WB + 2 * S_LB + S_STG + 1024;
+constexpr int S_ACC = 256;                         // tensor-memory columns per accumulator set (224 used)
+
+// The integer held by a level accumulator (FP32 bits, |value| < 2^24, exact).  Levels 0 and 1 stay within
+// 2^22 (64 products of at most 2^16, and 2 x 64 of at most 2^15), so adding 1.5 2^23 puts the integer in the
+// low mantissa bits (one FP32 add and one integer subtract); the lower levels take the conversion instruction.
+__device__ __forceinline__ long long level_int(uint32_t bits, int L) {
+  const float x = __uint_as_float(bits);
+  if (L <= 1) return (long long)(int)(__float_as_uint(x + 12582912.0f) - 0x4B400000u);
+  return (long long)__float2int_rn(x);
+}
+
+// Tiles of the trailing lower triangle handled by block b: strip ti, first column tile, count (0: nothing).
+__device__ inline void strip_chunk(int b, int part, int chunk, int& ti, int& first, int& count) {
+  constexpr int Q = K / SBN, CT = BM / SBN;
+  int cnt = 0;
+  for (ti = 0; ti < (1 << 20); ++ti) {
+    cnt = part == 1 ? Q : (part == 0 ? CT * (ti + 1) : CT * (ti + 1) - Q);
+    const int nch = (cnt + chunk - 1) / chunk;
+    if (b < nch) break;
+    b -= nch;
+  }
+  first = (part == 2 ? Q : 0) + b * chunk;
+  count = min(chunk, cnt - b * chunk);
+}
+
+__global__ void __launch_bounds__(640, 1) oz_strip_kernel(const __grid_constant__ OzMaps maps, double* __restrict__ A,
+                                                          int n, int k1, const int* __restrict__ ew,
+                                                          const int* __restrict__ el, int part, int chunk,
+                                                          unsigned* status) {
+  int ti, first, count;
+  strip_chunk(blockIdx.x, part, chunk, ti, first, count);
+  const int row0 = k1 + ti * BM;
+  count = min(count, (n - k1 + SBN - 1) / SBN - first);   // column tiles past n (ragged last strip) are skipped
+  if (row0 >= n || count <= 0) return;   // the whole CTA leaves before any barrier or allocation
+
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sW = smem;
+  uint8_t* sL = smem + S_WB;                                       // two buffers of S_LB
+  double* stage = reinterpret_cast<double*>(smem + S_WB + 2 * S_LB);
+  __shared__ __align__(8) uint64_t bar_w, lfull[2], lempty[2], afull[2], aempty[2], bar_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int w_issued, l_issued;
+  __shared__ int exp_w[BM];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar_w, 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&lfull[i], 1);
+      mbar_init(&lempty[i], 1);
+      mbar_init(&afull[i], 1);
+      mbar_init(&aempty[i], 16);
+    }
+    mbar_init(&bar_done, 1);
+    abort_flag = 0;
+    w_issued = 0;
+    l_issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int r = threadIdx.x; r < BM; r += blockDim.x) exp_w[r] = row0 + r < n ? ew[row0 + r] : 0;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(2u * S_ACC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: the strip's W digits once, then the L digits of each tile into buffer j % 2
+    mbar_expect_tx(&bar_w, (uint32_t)S_WB);
+    for (int s = 0; s < SS; ++s) tma_load_3d(&maps.w, &bar_w, sW + s * (BM * ROWB), 0, row0, s);
+    w_issued = 1;
+    int j = 0;
+    for (; j < count; ++j) {
+      const int lb = j & 1;
+      if (j >= 2 && !mbar_wait(&lempty[lb], (uint32_t)(j / 2 - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&lfull[lb], (uint32_t)S_LB);
+      const int col0 = k1 + (first + j) * SBN;
+      for (int t = 0; t < SS; ++t) tma_load_3d(&maps.l, &lfull[lb], sL + lb * S_LB + t * (SBN * ROWB), 0, col0, t);
+    }
+    l_issued = j;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: tile j's level s + t in columns (j % 2) S_ACC + (s + t) SBN
+    bool ok = mbar_wait(&bar_w, 0, &abort_flag);
+    const uint32_t w0 = smem_u32(sW);
+    for (int j = 0; ok && j < count; ++j) {
+      const int ab = j & 1;
+      if (j >= 2 && !mbar_wait(&aempty[ab], (uint32_t)(j / 2 - 1) & 1u, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      if (!mbar_wait(&lfull[ab], (uint32_t)(j / 2) & 1u, &abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // The L digit planes t = 0 .. 6 lie one after another in shared memory (32 rows each), so one MMA of
+      // N = 32 (7 - s) multiplies W digit s by L digits 0 .. 6 - s at once; its accumulator starts at level s,
+      // so the product with L digit t lands in level s + t.
+      const uint32_t l0 = smem_u32(sL + ab * S_LB);
+#pragma unroll
+      for (int s = 0; s < SS; ++s) {
+        const uint32_t id = idesc_bf16(BM, SBN * (SS - s));
+        const uint32_t d = tmem + (uint32_t)(ab * S_ACC + s * SBN);
+#pragma unroll
+        for (int kk = 0; kk < K / 16; ++kk)   // digit 0 of W is the first to reach every level
+          umma(d, sdesc(w0 + s * (BM * ROWB) + kk * 32), sdesc(l0 + kk * 32), id, (s > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&lempty[ab]);   // the L buffer is free once these MMAs have read it
+      umma_commit(&afull[ab]);    // and the accumulators are complete
+    }
+    if (!ok) abort_flag = 1;
+    umma_commit(&bar_done);   // arrives once every MMA issued above has completed
+  } else if (warp >= 4) {
+    // ---- epilogue: sixteen independent warps (no block-wide barrier, so that warps in their integer phase
+    // overlap warps in their FP64 phase); warp 4 + e drains tensor-memory lanes 32 (e % 4) .. + 31 (tile rows
+    // 32 (e % 4) + lane) and the 8 columns 8 (e / 4) .. + 7 of every level, stages that 32 x 8 block in its own
+    // shared-memory slot and updates it in A, four rows of 64 contiguous bytes per instruction.
+    const int e = warp - 4, wq = warp & 3, h = e >> 2;
+    const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    const int kr = exp_w[wq * 32 + lane] - SSHIFT;
+    double* st = stage + e * (32 * S_SLD);
+    const int rr = lane >> 3, cc = lane & 7;   // read-modify-write: rows 4 i + rr, column cc of the block
+    bool ok = true;
+    for (int j = 0; j < count; ++j) {
+      const int ab = j & 1;
+      const int c0 = k1 + (first + j) * SBN + 8 * h;   // first column of this warp's block
+      // A values of the block first: their latency hides behind the wait and the recombination
+      double cv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = row0 + wq * 32 + 4 * i + rr, col = c0 + cc;
+        cv[i] = (ok && row < n && col <= row) ? A[(long)row * n + col] : 0.0;
+      }
+      int el8[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) el8[c] = c0 + c < n ? __ldg(el + c0 + c) : 0;
+      if (ok) ok = __all_sync(0xffffffffu, mbar_wait(&afull[ab], (uint32_t)(j / 2) & 1u, &abort_flag));
+      tc_fence_after();
+      long long acc[8];
+      if (ok) {
+        // exact integer recombination N = sum_L acc_L 2^(SSHIFT - SBETA (L + 2)), every shift a constant
+        const uint32_t ta = tmem + lane_base + (uint32_t)(ab * S_ACC + 8 * h);
+        uint32_t v[32];
+        tmem_ld8_at<0>(ta + 0 * SBN, v);
+        tmem_ld8_at<8>(ta + 1 * SBN, v);
+        tmem_ld8_at<16>(ta + 2 * SBN, v);
+        tmem_ld8_at<24>(ta + 3 * SBN, v);
+        tmem_wait_ld1(v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          acc[c] = level_int(v[c], 0) * (1LL << (SSHIFT - 2 * SBETA)) +
+                   level_int(v[8 + c], 1) * (1LL << (SSHIFT - 3 * SBETA)) +
+                   level_int(v[16 + c], 2) * (1LL << (SSHIFT - 4 * SBETA)) +
+                   level_int(v[24 + c], 3) * (1LL << (SSHIFT - 5 * SBETA));
+        tmem_ld8_at<0>(ta + 4 * SBN, v);
+        tmem_ld8_at<8>(ta + 5 * SBN, v);
+        tmem_ld8_at<16>(ta + 6 * SBN, v);
+        tmem_wait_ld1(v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          acc[c] += level_int(v[c], 4) * (1LL << (SSHIFT - 6 * SBETA)) + level_int(v[8 + c], 5) +   // 2^0
+                    ((level_int(v[16 + c], 6) + 128) >> 8);                                        // 2^-8, rounded
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (ok && lane == 0) mbar_arrive(&aempty[ab]);   // the MMAs of tile j + 2 may overwrite this set
+      if (ok) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) st[lane * S_SLD + c] = scaled_int64(acc[c], kr + el8[c]);
+      }
+      __syncwarp();
+      if (ok) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int row = row0 + wq * 32 + 4 * i + rr, col = c0 + cc;
+          if (row < n && col <= row) A[(long)row * n + col] = cv[i] - st[(4 * i + rr) * S_SLD + cc];
+        }
+      }
+      __syncwarp();   // the slot is read before the next tile overwrites it
+    }
+    if (!ok) abort_flag = 1;
+  }
+  __syncwarp();
+
+  const bool done_ok = mbar_wait(&bar_done, 0, nullptr);
+  tc_fence_after();
+  const bool good = __syncthreads_and(done_ok ? 1 : 0) && !abort_flag;
+  if (threadIdx.x == 0 && !good) {
+    raise_status(status, DEV_ERR_TIMEOUT);
+    // no copy may land after the CTA exits: the W digits and the (at most two) L loads not known to be consumed
+    if (w_issued) mbar_wait(&bar_w, 0, nullptr);
+    for (int j = l_issued > 2 ? l_issued - 2 : 0; j < l_issued; ++j)
+      mbar_wait(&lfull[j & 1], (uint32_t)(j / 2) & 1u, nullptr);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * S_ACC) : "memory");
   }
 }
 
@@ -431,6 +662,27 @@ cdwac_status ozaki_update(cdwac_ctx* ctx, const OzakiPlan& plan, int buf, T* A, 
   using C = OzCfg<CPLX>;
   const int k1 = k0 + K, rows = n - k1;
   if (rows <= 0) return CDWAC_OK;
+  if constexpr (!CPLX) {
+    // row strips in chunks of about (tiles / SMs) tiles: one wave of CTAs, each loading its W digits once
+    const long mbs = (rows + BM - 1) / BM, cts = BM / SBN, qs = K / SBN;
+    const long all = cts * mbs * (mbs + 1) / 2;
+    const long tiles = part == 0 ? all : (part == 1 ? qs * mbs : all - qs * mbs);
+    if (tiles <= 0) return CDWAC_OK;
+    const int chunk = (int)std::min<long>(32, std::max<long>(1, (tiles + ctx->num_sms - 1) / ctx->num_sms));
+    long grid = 0;
+    for (long t = 0; t < mbs; ++t) {
+      const long cnt = part == 1 ? qs : (part == 0 ? cts * (t + 1) : cts * (t + 1) - qs);
+      grid += (cnt + chunk - 1) / chunk;
+    }
+    OzMaps maps;
+    maps.w = plan.wmap[buf];
+    maps.l = plan.lmap[buf];
+    CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(oz_strip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, S_SMEM));
+    oz_strip_kernel<<<(unsigned)grid, 640, S_SMEM, st>>>(maps, reinterpret_cast<double*>(A), n, k1, plan.ew[buf],
+                                                         plan.el[buf], part, chunk, ctx->d_status);
+    CDWAC_LAUNCH_CHECK(ctx);
+    return CDWAC_OK;
+  } else {
   const long mb = (rows + BM - 1) / BM, ct = BM / C::BN, q = K / C::BN;
   const long all = ct * mb * (mb + 1) / 2;
   const long tiles = part == 0 ? all : (part == 1 ? q * mb : all - q * mb);
@@ -443,10 +695,11 @@ cdwac_status ozaki_update(cdwac_ctx* ctx, const OzakiPlan& plan, int buf, T* A, 
                                            C::SMEM));
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(oz_update_kernel<CPLX>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
-  oz_update_kernel<CPLX><<<(unsigned)grid, 256, C::SMEM, st>>>(maps, A, n, k1, plan.ew[buf], plan.el[buf], part,
+  oz_update_kernel<CPLX><<<(unsigned)grid, C::NT, C::SMEM, st>>>(maps, A, n, k1, plan.ew[buf], plan.el[buf], part,
                                                               ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
+  }
 }
 
 template cdwac_status ozaki_slice<double>(cdwac_ctx*, const OzakiPlan&, int, const double*, int, int, const double*,

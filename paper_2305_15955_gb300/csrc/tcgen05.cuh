@@ -114,6 +114,16 @@ __device__ __forceinline__ void tmem_wait_ld16(uint32_t (&a)[16], uint32_t (&b)[
 }
 #undef CDWAC_R16
 
+// tcgen05.ld of 8 columns (this warp's 32 lanes) into r[OFF .. OFF + 7], without the wait; tmem_wait_ld1 then
+// orders up to four such loads into one 32-register array before any use of it.
+template <int OFF>
+__device__ __forceinline__ void tmem_ld8_at(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[OFF + 0]), "=r"(r[OFF + 1]), "=r"(r[OFF + 2]), "=r"(r[OFF + 3]), "=r"(r[OFF + 4]),
+                 "=r"(r[OFF + 5]), "=r"(r[OFF + 6]), "=r"(r[OFF + 7])
+               : "r"(taddr));
+}
+
 // tcgen05.ld of 32 columns without the wait: several loads may be in flight before one tmem_wait_ld.
 __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -134,6 +144,9 @@ __device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&r)[32
 __device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[32], uint32_t (&b)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" : CDWAC_R32(a)::"memory");
   asm volatile("" : CDWAC_R32(b)::"memory");   // ordered after the wait (volatile asm keeps its order)
+}
+__device__ __forceinline__ void tmem_wait_ld1(uint32_t (&a)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : CDWAC_R32(a)::"memory");
 }
 #undef CDWAC_R32
 
