@@ -305,10 +305,10 @@ constexpr int S_ACC = 256;                         // tensor-memory columns per 
 // The integer held by a level accumulator (FP32 bits, |value| < 2^24, exact).  Levels 0 and 1 stay within
 // 2^22 (64 products of at most 2^16, and 2 x 64 of at most 2^15), so adding 1.5 2^23 puts the integer in the
 // low mantissa bits (one FP32 add and one integer subtract); the lower levels take the conversion instruction.
-__device__ __forceinline__ long long level_int(uint32_t bits, int L) {
+__device__ __forceinline__ int level_int(uint32_t bits, int L) {
   const float x = __uint_as_float(bits);
-  if (L <= 1) return (long long)(int)(__float_as_uint(x + 12582912.0f) - 0x4B400000u);
-  return (long long)__float2int_rn(x);
+  if (L <= 1) return (int)(__float_as_uint(x + 12582912.0f) - 0x4B400000u);
+  return __float2int_rn(x);
 }
 
 // Tiles of the trailing lower triangle handled by block b: strip ti, first column tile, count (0: nothing).
@@ -450,7 +450,10 @@ __global__ void __launch_bounds__(640, 1) oz_strip_kernel(const __grid_constant_
       tc_fence_after();
       long long acc[8];
       if (ok) {
-        // exact integer recombination N = sum_L acc_L 2^(SSHIFT - SBETA (L + 2)), every shift a constant
+        // exact integer recombination N = sum_L a_L 2^(40 - 8 L) (SSHIFT = 56, SBETA = 8): levels 0 and 1 only
+        // reach the high word (a_0 2^8 + a_1 < 2^31), levels 2-5 are 32 x 32 -> 64-bit multiply-adds by
+        // constant powers of two, level 6 is rounded to 2^-8
+        static_assert(SSHIFT == 56 && SBETA == 8 && SS == 7, "recombination written for 7 x 8-bit digits");
         const uint32_t ta = tmem + lane_base + (uint32_t)(ab * S_ACC + 8 * h);
         uint32_t v[32];
         tmem_ld8_at<0>(ta + 0 * SBN, v);
@@ -459,19 +462,19 @@ __global__ void __launch_bounds__(640, 1) oz_strip_kernel(const __grid_constant_
         tmem_ld8_at<24>(ta + 3 * SBN, v);
         tmem_wait_ld1(v);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
-          acc[c] = level_int(v[c], 0) * (1LL << (SSHIFT - 2 * SBETA)) +
-                   level_int(v[8 + c], 1) * (1LL << (SSHIFT - 3 * SBETA)) +
-                   level_int(v[16 + c], 2) * (1LL << (SSHIFT - 4 * SBETA)) +
-                   level_int(v[24 + c], 3) * (1LL << (SSHIFT - 5 * SBETA));
+        for (int c = 0; c < 8; ++c) {
+          const int hi = level_int(v[c], 0) * 256 + level_int(v[8 + c], 1);
+          acc[c] = (long long)((unsigned long long)(unsigned)hi << 32) + (long long)level_int(v[16 + c], 2) * (1 << 24) +
+                   (long long)level_int(v[24 + c], 3) * (1 << 16);
+        }
         tmem_ld8_at<0>(ta + 4 * SBN, v);
         tmem_ld8_at<8>(ta + 5 * SBN, v);
         tmem_ld8_at<16>(ta + 6 * SBN, v);
         tmem_wait_ld1(v);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
-          acc[c] += level_int(v[c], 4) * (1LL << (SSHIFT - 6 * SBETA)) + level_int(v[8 + c], 5) +   // 2^0
-                    ((level_int(v[16 + c], 6) + 128) >> 8);                                        // 2^-8, rounded
+          acc[c] += (long long)level_int(v[c], 4) * (1 << 8) + (long long)level_int(v[8 + c], 5) +
+                    (long long)((level_int(v[16 + c], 6) + 128) >> 8);
       }
       tc_fence_before();
       __syncwarp();
