@@ -99,6 +99,18 @@ __device__ inline double scaled_int64(long long a, int k) {
   return __longlong_as_double((long long)(sgn | (((unsigned long long)(E - 1) << 52) + m)));
 }
 
+// The integer held by a level accumulator (FP32 bits of an integer below 2^24, exact).  fint22: for values
+// within 2^22, adding 1.5 2^23 puts the integer in the low mantissa bits (one FP32 add and one integer subtract
+// instead of the conversion instruction).  Real digits keep levels 0 and 1 within 2^22 (64 products of at most
+// 2^16, and 2 x 64 of at most 2^15), complex digits levels 0-5 (at most 6 x 128 products of at most 2^13 or
+// 2^14).
+__device__ __forceinline__ int fint22(uint32_t bits) {
+  return (int)(__float_as_uint(__uint_as_float(bits) + 12582912.0f) - 0x4B400000u);
+}
+__device__ __forceinline__ int level_int(uint32_t bits, int L) {
+  return L <= 1 ? fint22(bits) : __float2int_rn(__uint_as_float(bits));
+}
+
 // One CTA per 128 x 32 tile of the trailing lower triangle (complex: two CTAs per tile, one per part of A), two
 // CTAs per SM, so that one CTA's epilogue (tensor-memory drain, integer recombination, read-modify-write of A)
 // overlaps the other's loads and MMAs.  The L digits of the tile stay in shared memory; the W digits stream
@@ -180,7 +192,6 @@ __global__ void __launch_bounds__(OzCfg<CPLX>::NT, OzCfg<CPLX>::MIN_CTAS) oz_upd
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer: W digit s (part ph) times L digit t of the paired part accumulates in level s + t, columns
     // (s + t) BN.  Real: W L.  Complex, re CTA: Wr Lr - Wi Li (negated-A descriptor); im CTA: Wr Li + Wi Lr.
-    constexpr uint32_t id = idesc_bf16(BM, BN);
     bool ok = mbar_wait(&bar_l, 0, &abort_flag);
     int q = 0;
     if (ok) {
@@ -195,14 +206,14 @@ __global__ void __launch_bounds__(OzCfg<CPLX>::NT, OzCfg<CPLX>::MIN_CTAS) oz_upd
         const int ph = q / S, s = q % S;
         const int lp = CPLX ? (ph ^ pr) : 0;
         const uint32_t neg = (CPLX && ph == 1 && pr == 0) ? NEG_A : 0u;
-        const uint32_t abase = a0 + st * C::A_TILE;
-        for (int t = 0; s + t < S; ++t) {
-          const uint32_t d = tmem + (uint32_t)((s + t) * BN);
-          const uint32_t bbase = b0 + (lp * S + t) * C::B_TILE;
+        // the L digit planes t = 0 .. S - 1 of part lp lie one after another (BN rows each): one MMA of
+        // N = BN (S - s) multiplies W digit s by L digits 0 .. S - 1 - s, its accumulator starting at level s
+        const uint32_t abase = a0 + st * C::A_TILE, bbase = b0 + lp * S * C::B_TILE;
+        const uint32_t idn = idesc_bf16(BM, BN * (S - s)) | neg;
+        const uint32_t d = tmem + (uint32_t)(s * BN);
 #pragma unroll
-          for (int kk = 0; kk < K / 16; ++kk)   // q = 0 (digit 0 of Wr) is the first to reach every level
-            umma(d, sdesc(abase + kk * 32), sdesc(bbase + kk * 32), id | neg, (q > 0 || kk > 0) ? 1u : 0u);
-        }
+        for (int kk = 0; kk < K / 16; ++kk)   // q = 0 (digit 0 of Wr) is the first to reach every level
+          umma(d, sdesc(abase + kk * 32), sdesc(bbase + kk * 32), idn, (q > 0 || kk > 0) ? 1u : 0u);
         umma_commit(&empty_bar[st]);   // the stage is free once these MMAs have read it
       }
     }
@@ -223,58 +234,65 @@ __global__ void __launch_bounds__(OzCfg<CPLX>::NT, OzCfg<CPLX>::MIN_CTAS) oz_upd
     for (int q = w_consumed; q < w_issued; ++q) mbar_wait(&full_bar[q % NS], (uint32_t)(q / NS) & 1u, nullptr);
   }
   if (good) {
-    // Every MMA has completed, so the operand buffers are free for staging the update, [128 rows][BN + 1].
-    // Drain: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and 16 columns, 16 (w / 4) .. + 15.
-    // Read-modify-write: warp w updates tile rows RW w .. RW w + RW - 1, 32 / BN rows per instruction with lane =
-    // (row, column), coalesced row segments (the other CTAs on the SM hide the latency of its loads).
-    constexpr int NW = C::NT / 32, SLD = BN + 1, RW = BM / NW, RPP = 32 / BN;
-    static_assert(BN / (NW / 4) == 16, "sixteen accumulator columns per thread");
+    // Every MMA has completed, so the operand buffers are free: each warp stages its own 32 x 16 block there.
+    // Warp w drains tensor-memory lanes 32 (w % 4) .. + 31 (tile rows 32 (w % 4) + lane) and the 16 columns
+    // 16 (w / 4) .. + 15 of every level, recombines them exactly, and updates its block of A (part pr), two rows of
+    // 16 columns per instruction; no block-wide barrier, so the warps' integer and FP64 phases overlap.
+    static_assert(CPLX && S == 8 && BETA == 7 && C::SHIFT == 55 && BN == 32 && C::NT == 256,
+                  "recombination written for complex 8 x 7-bit digits, 32-column tiles and eight warps");
     double* Ad = reinterpret_cast<double*>(A_out);
-    constexpr long ES = CPLX ? 2 : 1;   // doubles per element of A
-    double* stage = reinterpret_cast<double*>(smem);
     const int wq = warp & 3, h = warp >> 2;
     const uint32_t lane_base = (uint32_t)(wq * 32) << 16;
+    double* stw = reinterpret_cast<double*>(smem) + warp * (32 * 17);
+    const int rr = lane >> 4, cc = lane & 15, c0 = col0 + 16 * h;
+    // N = sum_L a_L 2^(41 - 7 L): levels 0 and 1 only reach the high word (a_0 2^9 + a_1 2^2 < 2^31), levels 2-5
+    // are 32 x 32 -> 64-bit multiply-adds by constant powers of two, levels 6 and 7 are rounded to 2^-1 and 2^-8
+    long long acc[16];
     {
-      // exact integer recombination N = sum_L acc_L 2^(SHIFT - BETA (L + 2)) on the integer pipe (bits of the
-      // lowest levels below 2^-SHIFT are rounded off, < 2^-60 of the largest term)
-      long long acc[16];
+      const uint32_t ta = tmem + lane_base + (uint32_t)(16 * h);
+      uint32_t v0[16], v1[16];
+      tmem_ld16_async(ta + 0 * BN, v0);
+      tmem_ld16_async(ta + 1 * BN, v1);
+      tmem_wait_ld16(v0, v1);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) acc[j] = 0;
-      auto add_level = [&](const uint32_t(&v)[16], int L) {
-        const int sh = C::SHIFT - BETA * (L + 2);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const long long a = (long long)__float2int_rn(__uint_as_float(v[j]));   // exact: an integer < 2^24
-          acc[j] += sh >= 0 ? (a << sh) : ((a + (1LL << (-sh - 1))) >> -sh);   // rounded, not floored
-        }
-      };
-#pragma unroll 1
-      for (int L = 0; L < S; L += 2) {
-        uint32_t v0[16], v1[16];
-        tmem_ld16_async(tmem + lane_base + (uint32_t)(L * BN + 16 * h), v0);
-        if (L + 1 < S) tmem_ld16_async(tmem + lane_base + (uint32_t)((L + 1) * BN + 16 * h), v1);
-        tmem_wait_ld16(v0, v1);
-        add_level(v0, L);
-        if (L + 1 < S) add_level(v1, L + 1);
+      for (int c = 0; c < 16; ++c) {
+        const int hi = fint22(v0[c]) * 512 + fint22(v1[c]) * 4;
+        acc[c] = (long long)((unsigned long long)(unsigned)hi << 32);
       }
-      // staged: the scaled update N 2^(e_row + e_col - SHIFT) of element (tile row wq * 32 + lane, column 16 h + j)
-      double* st = stage + (wq * 32 + lane) * SLD + 16 * h;
-      const int kr = exp_w[wq * 32 + lane] - C::SHIFT;
+      tmem_ld16_async(ta + 2 * BN, v0);
+      tmem_ld16_async(ta + 3 * BN, v1);
+      tmem_wait_ld16(v0, v1);
 #pragma unroll
-      for (int j = 0; j < 16; ++j) st[j] = scaled_int64(acc[j], kr + exp_l[16 * h + j]);
+      for (int c = 0; c < 16; ++c)
+        acc[c] += (long long)fint22(v0[c]) * (1 << 27) + (long long)fint22(v1[c]) * (1 << 20);
+      tmem_ld16_async(ta + 4 * BN, v0);
+      tmem_ld16_async(ta + 5 * BN, v1);
+      tmem_wait_ld16(v0, v1);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        acc[c] += (long long)fint22(v0[c]) * (1 << 13) + (long long)fint22(v1[c]) * (1 << 6);
+      tmem_ld16_async(ta + 6 * BN, v0);
+      tmem_ld16_async(ta + 7 * BN, v1);
+      tmem_wait_ld16(v0, v1);
+#pragma unroll
+      for (int c = 0; c < 16; ++c)
+        acc[c] += (long long)((__float2int_rn(__uint_as_float(v0[c])) + 1) >> 1) +
+                  (long long)((__float2int_rn(__uint_as_float(v1[c])) + 128) >> 8);
     }
-    __syncthreads();
-    const int rsub = lane / BN, col = col0 + lane % BN;
-    double cv[RW / RPP];
+    const int kr = exp_w[wq * 32 + lane] - C::SHIFT;
 #pragma unroll
-    for (int p = 0; p < RW / RPP; ++p) {
-      const int row = row0 + RW * warp + RPP * p + rsub;
-      cv[p] = (row < n && col <= row) ? Ad[((long)row * n + col) * ES + pr] : 0.0;
+    for (int c = 0; c < 16; ++c) stw[lane * 17 + c] = scaled_int64(acc[c], kr + exp_l[16 * h + c]);
+    __syncwarp();
+    double cv[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int row = row0 + wq * 32 + 2 * i + rr, col = c0 + cc;
+      cv[i] = (row < n && col <= row) ? Ad[((long)row * n + col) * 2 + pr] : 0.0;
     }
 #pragma unroll
-    for (int p = 0; p < RW / RPP; ++p) {
-      const int r = RW * warp + RPP * p + rsub, row = row0 + r;
-      if (row < n && col <= row) Ad[((long)row * n + col) * ES + pr] = cv[p] - stage[r * SLD + lane % BN];
+    for (int i = 0; i < 16; ++i) {
+      const int row = row0 + wq * 32 + 2 * i + rr, col = c0 + cc;
+      if (row < n && col <= row) Ad[((long)row * n + col) * 2 + pr] = cv[i] - stw[(2 * i + rr) * 17 + cc];
     }
   }
   tc_fence_before();
@@ -301,15 +319,6 @@ constexpr int S_SLD = 9;                           // staging row stride (double
 constexpr int S_STG = 16 * 32 * S_SLD * 8;         // a 32 x 8 slot per epilogue warp: 36 KB
 constexpr int S_SMEM = S_WB + 2 * S_LB + S_STG + 1024;
 constexpr int S_ACC = 256;                         // tensor-memory columns per accumulator set (224 used)
-
-// The integer held by a level accumulator (FP32 bits, |value| < 2^24, exact).  Levels 0 and 1 stay within
-// 2^22 (64 products of at most 2^16, and 2 x 64 of at most 2^15), so adding 1.5 2^23 puts the integer in the
-// low mantissa bits (one FP32 add and one integer subtract); the lower levels take the conversion instruction.
-__device__ __forceinline__ int level_int(uint32_t bits, int L) {
-  const float x = __uint_as_float(bits);
-  if (L <= 1) return (int)(__float_as_uint(x + 12582912.0f) - 0x4B400000u);
-  return __float2int_rn(x);
-}
 
 // Tiles of the trailing lower triangle handled by block b: strip ti, first column tile, count (0: nothing).
 __device__ inline void strip_chunk(int b, int part, int chunk, int& ti, int& first, int& count) {
