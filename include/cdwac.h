@@ -294,17 +294,21 @@ typedef struct {
 } cdwac_batch_item;
 
 #define CDWAC_BATCH_GRAPH 1u     /* capture the whole batch into one CUDA graph and replay it */
-#define CDWAC_BATCH_AUTOTUNE 2u  /* choose lanes and LDL^T lookahead by timing candidates (cached per size bucket) */
+#define CDWAC_BATCH_AUTOTUNE 2u  /* choose lanes, LDL^T lookahead and tile configuration by timing candidates
+                                    (cached per size bucket) */
 
 /* CD-WAC for many systems of uneven size in one stream-ordered call: the systems are spread over up to
  * `max_lanes` concurrent lanes (streams with their own scratch), largest first, and each runs W(i xi), the
  * near-real points, the Thiele fits, Sigma on its grid and the QP equation.  With CDWAC_BATCH_GRAPH the batch is
  * captured once into a CUDA graph (keyed on the item array's contents) and later calls with the same items
  * replay it: the items' buffers must stay valid.  With CDWAC_BATCH_AUTOTUNE the first call for a size bucket
- * times every lane count in {1, 2, 4, 8} <= max_lanes with and without the LDL^T lookahead and keeps the fastest;
- * choices are appended to the file named by the environment variable CDWAC_TUNE_CACHE (if set) and read back by
- * later processes.  `chosen` (may be NULL) receives {lanes, lookahead}.  The precision and parameters are the
- * same for every item. */
+ * times every lane count in {1, 2, 4, 8} <= max_lanes with and without the LDL^T lookahead, then, from the
+ * fastest, the tile configuration of the tensor-core kernels: the Pi tile-group size (the 128 x 128 output tiles
+ * are ordered in G x G groups; G in {4, 8, 12, 16}) and the number of CTA waves (1, 2 or 3) the real trailing
+ * update's 128-row strips are cut into; it keeps the fastest.  None of these choices changes any result.  Choices
+ * are appended to the file named by the environment variable CDWAC_TUNE_CACHE (if set) and read back by later
+ * processes.  `chosen` (may be NULL; four ints) receives {lanes, lookahead, Pi tile-group size, update waves}.
+ * The precision and parameters are the same for every item. */
 cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items, const cdwac_params* prm,
                              double tol, int max_iter, int max_lanes, unsigned flags, int* chosen, void* stream);
 

@@ -493,18 +493,19 @@ class BatchResult:
 
 def batch_run(ctx: "Context", results, params: Params, max_lanes=4, graph=False, autotune=False, tol=1e-7,
               max_iter=100, sync=True, items=None):
-    """cdwac_batch_run over BatchResult objects; returns (lanes, lookahead) the call used and the ctypes items
-    (pass them back as `items` to replay a captured graph with the identical item array)."""
+    """cdwac_batch_run over BatchResult objects; returns (lanes, lookahead, Pi tile-group size, update waves) the
+    call used and the ctypes items (pass them back as `items` to replay a captured graph with the identical item
+    array)."""
     if items is None:
         items = (_BatchItem * len(results))(*[r.c() for r in results])
     p = params.c()
-    chosen = (ctypes.c_int * 2)()
+    chosen = (ctypes.c_int * 4)()
     flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
     ctx._check(ctx.lib.cdwac_batch_run(ctx.h, items, len(results), ctypes.byref(p), float(tol), int(max_iter),
                                        int(max_lanes), flags, chosen, ctx._stream()))
     if sync:
         ctx.sync_status(allow=(ERR_PADE_BREAKDOWN, ERR_QP_NOT_CONVERGED))
-    return (int(chosen[0]), int(chosen[1])), items
+    return tuple(int(c) for c in chosen), items
 
 
 def build_W_imag_noalloc(system: System, params: Params, xi, wxi, W_imag, dev_status=None, stream=None) -> int:

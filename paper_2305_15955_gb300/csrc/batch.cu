@@ -5,7 +5,10 @@
 // device status word.  The caller's stream forks to the lanes through one event and joins them back, so the
 // whole batch is one stream-ordered unit that can be captured into a CUDA graph: with CDWAC_BATCH_GRAPH the first
 // call runs eagerly (sizing every lane's scratch), captures the same sequence, and later calls with identical
-// items replay the graph.  The autotuner times lane counts and the lookahead switch per size bucket.
+// items replay the graph.  The autotuner times, per size bucket, lane counts and the lookahead switch, then the tile
+// configuration of the tensor-core kernels: the Pi tile-group size (the rasterisation of the 128 x 128 output
+// tiles over the waves) and the number of CTA waves the real trailing update's row strips are cut into (the
+// number of 128 x 32 tiles each CTA streams against its resident W digits).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -22,6 +25,8 @@ namespace {
 struct Config {
   int lanes;
   int lookahead;
+  int pi_group;    // Pi tile-group size (cdwac_ctx::pi_group)
+  int upd_waves;   // real trailing update: CTA waves of row-strip chunks (cdwac_ctx::upd_waves)
 };
 
 double item_cost(const cdwac_batch_item& it, const cdwac_params* p) {
@@ -104,6 +109,8 @@ cdwac_status enqueue(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items,
     if (lane_items[l].empty()) continue;
     cdwac_ctx* lane = ctx->lanes[l];
     lane->side_stream = cfg.lookahead ? lane->own_side : nullptr;
+    lane->pi_group = cfg.pi_group;
+    lane->upd_waves = cfg.upd_waves;
     lane->prof = 0;
     cudaStream_t s = ctx->lane_streams[l];
     CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(s, ctx->ev_fork, 0));
@@ -137,7 +144,7 @@ std::string bucket_of(const cdwac_batch_item* items, int n_items, const cdwac_pa
     nmax = std::max(nmax, items[i].sys.n_aux);
   }
   char buf[128];
-  snprintf(buf, sizeof(buf), "n%d_c%d_a%d_p%d", n_items, (int)std::floor(std::log2(total + 1.0)),
+  snprintf(buf, sizeof(buf), "t2_n%d_c%d_a%d_p%d", n_items, (int)std::floor(std::log2(total + 1.0)),
            (int)std::floor(std::log2((double)nmax + 1.0)), prm->precision);
   return buf;
 }
@@ -148,12 +155,12 @@ bool cache_lookup(const std::string& bucket, int max_lanes, Config* cfg) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char b[128];
-  int lanes, la;
+  int lanes, la, pg, uw;
   double ms;
   bool found = false;
-  while (fscanf(f, "%127s %d %d %lf", b, &lanes, &la, &ms) == 4)
-    if (bucket == b && lanes <= max_lanes) {
-      *cfg = {lanes, la};
+  while (fscanf(f, "%127s %d %d %d %d %lf", b, &lanes, &la, &pg, &uw, &ms) == 6)
+    if (bucket == b && lanes <= max_lanes && pg >= 1 && pg <= 64 && uw >= 1 && uw <= 8) {
+      *cfg = {lanes, la, pg, uw};
       found = true;
     }
   fclose(f);
@@ -165,7 +172,7 @@ void cache_store(const std::string& bucket, Config cfg, double ms) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %.3f\n", bucket.c_str(), cfg.lanes, cfg.lookahead, ms);
+  fprintf(f, "%s %d %d %d %d %.3f\n", bucket.c_str(), cfg.lanes, cfg.lookahead, cfg.pi_group, cfg.upd_waves, ms);
   fclose(f);
 }
 
@@ -191,7 +198,7 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
 
-  Config cfg{std::min(max_lanes, std::min(n_items, 4)), 1};
+  Config cfg{std::min(max_lanes, std::min(n_items, 4)), 1, ctx->pi_group, ctx->upd_waves};
   if (flags & CDWAC_BATCH_AUTOTUNE) {
     const std::string bucket = bucket_of(items, n_items, prm);
     bool have = false;
@@ -207,24 +214,45 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
       CDWAC_CUDA_TRY(ctx, cudaEventCreate(&t1));
       double best = 1e300;
       Config best_cfg = cfg;
+      // one warm run (sizes scratch), one timed run; keeps the fastest
+      auto trial = [&](Config c) -> cdwac_status {
+        cdwac_status rc = enqueue(ctx, items, n_items, prm, tol, max_iter, c, st);
+        if (rc) return rc;
+        CDWAC_CUDA_TRY(ctx, cudaEventRecord(t0, st));
+        rc = enqueue(ctx, items, n_items, prm, tol, max_iter, c, st);
+        if (rc) return rc;
+        CDWAC_CUDA_TRY(ctx, cudaEventRecord(t1, st));
+        CDWAC_CUDA_TRY(ctx, cudaEventSynchronize(t1));
+        float ms = 0.f;
+        CDWAC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, t0, t1));
+        if (ms < best) {
+          best = ms;
+          best_cfg = c;
+        }
+        return CDWAC_OK;
+      };
+      // stage 1: lanes x lookahead at the current tile configuration
       for (int lanes : {1, 2, 4, 8}) {
         if (lanes > max_lanes || lanes > n_items) continue;
         for (int la = 0; la < 2; ++la) {
-          Config c{lanes, la};
-          cdwac_status rc = enqueue(ctx, items, n_items, prm, tol, max_iter, c, st);   // warm (sizes scratch)
+          cdwac_status rc = trial(Config{lanes, la, cfg.pi_group, cfg.upd_waves});
           if (rc) return rc;
-          CDWAC_CUDA_TRY(ctx, cudaEventRecord(t0, st));
-          rc = enqueue(ctx, items, n_items, prm, tol, max_iter, c, st);
-          if (rc) return rc;
-          CDWAC_CUDA_TRY(ctx, cudaEventRecord(t1, st));
-          CDWAC_CUDA_TRY(ctx, cudaEventSynchronize(t1));
-          float ms = 0.f;
-          CDWAC_CUDA_TRY(ctx, cudaEventElapsedTime(&ms, t0, t1));
-          if (ms < best) {
-            best = ms;
-            best_cfg = c;
-          }
         }
+      }
+      // stage 2: Pi tile-group size; stage 3: row-strip waves of the real trailing update (each from the best so far)
+      for (int g : {4, 8, 16}) {
+        Config c = best_cfg;
+        if (g == c.pi_group) continue;
+        c.pi_group = g;
+        cdwac_status rc = trial(c);
+        if (rc) return rc;
+      }
+      for (int w : {1, 2, 3}) {
+        Config c = best_cfg;
+        if (w == c.upd_waves) continue;
+        c.upd_waves = w;
+        cdwac_status rc = trial(c);
+        if (rc) return rc;
       }
       cudaEventDestroy(t0);
       cudaEventDestroy(t1);
@@ -236,6 +264,8 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
   if (chosen) {
     chosen[0] = cfg.lanes;
     chosen[1] = cfg.lookahead;
+    chosen[2] = cfg.pi_group;
+    chosen[3] = cfg.upd_waves;
   }
 
   if (!(flags & CDWAC_BATCH_GRAPH)) return enqueue(ctx, items, n_items, prm, tol, max_iter, cfg, st);

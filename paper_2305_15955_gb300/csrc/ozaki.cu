@@ -675,12 +675,14 @@ cdwac_status ozaki_update(cdwac_ctx* ctx, const OzakiPlan& plan, int buf, T* A, 
   const int k1 = k0 + K, rows = n - k1;
   if (rows <= 0) return CDWAC_OK;
   if constexpr (!CPLX) {
-    // row strips in chunks of about (tiles / SMs) tiles: one wave of CTAs, each loading its W digits once
+    // row strips in chunks of about tiles / (SMs x upd_waves) tiles: upd_waves waves of CTAs (1 unless the batch
+    // autotuner chose more), each loading its W digits once
     const long mbs = (rows + BM - 1) / BM, cts = BM / SBN, qs = K / SBN;
     const long all = cts * mbs * (mbs + 1) / 2;
     const long tiles = part == 0 ? all : (part == 1 ? qs * mbs : all - qs * mbs);
     if (tiles <= 0) return CDWAC_OK;
-    const int chunk = (int)std::min<long>(32, std::max<long>(1, (tiles + ctx->num_sms - 1) / ctx->num_sms));
+    const long slots = (long)ctx->num_sms * std::max(1, std::min(8, ctx->upd_waves));
+    const int chunk = (int)std::min<long>(32, std::max<long>(1, (tiles + slots - 1) / slots));
     long grid = 0;
     for (long t = 0; t < mbs; ++t) {
       const long cnt = part == 1 ? qs : (part == 0 ? cts * (t + 1) : cts * (t + 1) - qs);

@@ -44,10 +44,9 @@ __device__ inline void lower_tile_coords(int b, int& ti, int& tj) {
 
 // Tile b of the lower triangle of nt x nt tiles, in groups of G x G tiles (lower-triangle order of the groups,
 // row-major inside a group): the CTAs of one wave then share about 2G operand row blocks, so that each K-slice of
-// them comes from DRAM once per wave instead of once per row block of the whole triangle.
-constexpr int TILE_GROUP = 12;
-__device__ inline void grouped_tile_coords(int b, int nt, int& ti, int& tj) {
-  constexpr int G = TILE_GROUP;
+// them comes from DRAM once per wave instead of once per row block of the whole triangle.  G is the context's
+// pi_group (12 unless the batch autotuner chose another).
+__device__ inline void grouped_tile_coords(int b, int nt, int G, int& ti, int& tj) {
   const int ns = (nt + G - 1) / G;
   int rem = b;
   for (int I = 0; I < ns; ++I) {
@@ -97,7 +96,8 @@ constexpr int TMEM_COLS = (NHH + 1) * BN;          // and the correction accumul
 // Warps: 0 = TMA producer (lane 0), 1 = tensor-memory owner and MMA issuer (lane 0), 4..11 = two drain warpgroups
 // (warp w reads tensor-memory lanes 32 (w % 4) .. + 31, the tile rows it later writes); 2, 3 idle.
 __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__ Maps maps, int n, int k_tiles,
-                                                         void* A_out, int part, float* negpi32, unsigned* status) {
+                                                         int group, void* A_out, int part, float* negpi32,
+                                                         unsigned* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nt = (n + BM - 1) / BM;
   int ti, tj;
-  grouped_tile_coords(blockIdx.x, nt, ti, tj);
+  grouped_tile_coords(blockIdx.x, nt, group, ti, tj);
   const int row0 = ti * BM, col0 = tj * BN;
   if (col0 >= n) return;   // past the triangle: the whole CTA leaves before any barrier or allocation
 
@@ -434,7 +434,9 @@ cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh,
     return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
   const int nt = (n + BM - 1) / BM;
-  tc_syrk_kernel<<<nt * (nt + 1) / 2, 384, SMEM, st>>>(maps, n, (int)(s.kpad / BK), A, part, negpi32, ctx->d_status);
+  const int group = ctx->pi_group >= 1 && ctx->pi_group <= 64 ? ctx->pi_group : 12;
+  tc_syrk_kernel<<<nt * (nt + 1) / 2, 384, SMEM, st>>>(maps, n, (int)(s.kpad / BK), group, A, part, negpi32,
+                                                        ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }
