@@ -113,3 +113,37 @@ def test_bad_arguments(ctx):
     assert ctx.lib.cdwac_ldlt_factor(ctx.h, cdwac._ptr(Ag), 4, 0, 7, None) == cdwac.ERR_ARG
     assert ctx.lib.cdwac_ldlt_factor(ctx.h, None, 4, 0, 0, None) == cdwac.ERR_ARG
     assert ctx.lib.cdwac_ldlt_factor(ctx.h, cdwac._ptr(Ag), 0, 0, 0, None) == cdwac.ERR_ARG
+
+
+@pytest.mark.parametrize("z,upd_waves", [(0.3j, 1), (0.3j, 3), (0.45 + 1e-3j, 1)])
+def test_full_size_factor_backward_error(z, upd_waves, monkeypatch):
+    """N_aux = 4000, the acene-like order, in the launch configuration the bench times (lookahead, row-strip chunks
+    of up to 14 tiles for the real update, per-tile complex update): the tensor-core factor is backward stable like
+    an FP64 factorisation (L D L^T reproduces A to 1e-13 of its largest entry).  Real SPD case: it also agrees with
+    the FP64-update factor to FP64 forward accuracy, with cond(A) <= ||A||_inf (the eigenvalues of I - Pi(i xi) are
+    at least 1).  upd_waves = 3 cuts the real update's strips into three waves of chunks (one of the autotuner's
+    choices) and must give the same factor bit for bit."""
+    monkeypatch.setenv("CDWAC_UPD_WAVES", str(upd_waves))
+    c = cdwac.Context(0)
+    n = 4000
+    A = i_minus_pi(n, z, seed=77)
+    try:
+        L, d, F = gpu_factor(c, A, cdwac.LDLT_EMULATED)
+        L1, d1, _ = gpu_factor(c, A, cdwac.LDLT_FP64)
+    finally:
+        c.close()
+    for Lx, dx in ((L, d), (L1, d1)):
+        back = np.max(np.abs((Lx * dx[None, :]) @ Lx.T - A)) / np.max(np.abs(A))
+        assert back <= 1e-13, back
+    if z.real == 0.0:
+        tol = max(TOL, 1e-16 * n * np.max(np.sum(np.abs(A), axis=1)))
+        assert np.max(np.abs(d - d1)) <= tol * np.max(np.abs(d1))
+        assert np.max(np.abs(L - L1)) <= tol * np.max(np.abs(L1))
+    if upd_waves != 1:
+        monkeypatch.setenv("CDWAC_UPD_WAVES", "1")
+        c2 = cdwac.Context(0)
+        try:
+            _, _, F2 = gpu_factor(c2, A, cdwac.LDLT_EMULATED)
+        finally:
+            c2.close()
+        assert np.array_equal(np.tril(F), np.tril(F2))
