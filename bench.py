@@ -203,7 +203,10 @@ def run_reference(args, rank, ws, dist):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc},
+            "config": {"workload": desc,
+                       "timing": "extrapolated: each step times the oracle's W(i xi) at one of the 100 imaginary "
+                                 "frequencies and scales it by 100 + 4 x 40 frequency-equivalents (a near-real point "
+                                 "is a complex build, about four real ones); the whole step is about 2000 s of CPU"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "W_nm(i xi) at 1 of 100 imaginary frequencies per step (numpy/OpenBLAS FP64), "
                                        "scaled by 100 + 4*40 points; fits and Sigma not counted (negligible)"},
