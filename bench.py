@@ -585,7 +585,7 @@ def run_batch(args, rank, ws, dist):
     l0 = ctx.launch_count()
     chosen, items = cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True,   # eager run + capture
                                     max_iter=args.qp_max_iter)
-    ln, la, pg, uw = chosen
+    ln, la, pg, pt, uw = chosen
     graph_kernels = (ctx.launch_count() - l0) // 2   # the eager run and the capture enqueue the same kernels
     for _ in range(max(0, args.warmup - 1)):
         cdwac.batch_run(ctx, res, prm, max_lanes=lanes, graph=True, items=items, sync=False,
@@ -614,7 +614,8 @@ def run_batch(args, rank, ws, dist):
             "config": {"workload": f"uneven batch: {len(specs)} systems, N_basis " +
                                    ",".join(str(sp.n_basis) for sp in specs) +
                                    ", N_aux = 3.3 N_basis, 4 core states each, one CUDA graph per step",
-                       "lanes": ln, "lookahead": la, "pi_tile_group": pg, "update_waves": uw,
+                       "lanes": ln, "lookahead": la, "pi_tile_group": pg, "pi_tile_width": pt,
+                       "update_waves": uw,
                        "n_states_total": n_states, "qp_max_iter": args.qp_max_iter,
                        "input_generation_s": t_gen},
             "pi_tflop_per_step": pi_flops / 1e12,

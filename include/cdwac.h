@@ -303,12 +303,14 @@ typedef struct {
  * captured once into a CUDA graph (keyed on the item array's contents) and later calls with the same items
  * replay it: the items' buffers must stay valid.  With CDWAC_BATCH_AUTOTUNE the first call for a size bucket
  * times every lane count in {1, 2, 4, 8} <= max_lanes with and without the LDL^T lookahead, then, from the
- * fastest, the tile configuration of the tensor-core kernels: the Pi tile-group size (the 128 x 128 output tiles
- * are ordered in G x G groups; G in {4, 8, 12, 16}) and the number of CTA waves (1, 2 or 3) the real trailing
- * update's 128-row strips are cut into; it keeps the fastest.  None of these choices changes any result.  Choices
- * are appended to the file named by the environment variable CDWAC_TUNE_CACHE (if set) and read back by later
- * processes.  `chosen` (may be NULL; four ints) receives {lanes, lookahead, Pi tile-group size, update waves}.
- * The precision and parameters are the same for every item. */
+ * fastest, the tile configuration of the tensor-core kernels: the Pi output tile width (128 x 256 or 128 x 128),
+ * its tile-group size (output tiles ordered in groups of G row blocks; G in {4, 8, 12, 16}) and the number of CTA
+ * waves (1, 2 or 3) the real trailing update's 128-row strips are cut into; it keeps the fastest.  The group size
+ * and the waves change no result bit; the two Pi tile widths sum the same products in a different order at the
+ * 2048-column chunk boundaries (FP32 rounding).  Choices are appended to the file named by the environment
+ * variable CDWAC_TUNE_CACHE (if set) and read back by later processes.  `chosen` (may be NULL; five ints)
+ * receives {lanes, lookahead, Pi tile-group size, Pi tile width, update waves}.  The precision and parameters
+ * are the same for every item. */
 cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items, const cdwac_params* prm,
                              double tol, int max_iter, int max_lanes, unsigned flags, int* chosen, void* stream);
 

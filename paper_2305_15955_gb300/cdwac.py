@@ -493,13 +493,13 @@ class BatchResult:
 
 def batch_run(ctx: "Context", results, params: Params, max_lanes=4, graph=False, autotune=False, tol=1e-7,
               max_iter=100, sync=True, items=None):
-    """cdwac_batch_run over BatchResult objects; returns (lanes, lookahead, Pi tile-group size, update waves) the
-    call used and the ctypes items (pass them back as `items` to replay a captured graph with the identical item
-    array)."""
+    """cdwac_batch_run over BatchResult objects; returns (lanes, lookahead, Pi tile-group size, Pi tile width,
+    update waves) the call used and the ctypes items (pass them back as `items` to replay a captured graph with the
+    identical item array)."""
     if items is None:
         items = (_BatchItem * len(results))(*[r.c() for r in results])
     p = params.c()
-    chosen = (ctypes.c_int * 4)()
+    chosen = (ctypes.c_int * 5)()
     flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
     ctx._check(ctx.lib.cdwac_batch_run(ctx.h, items, len(results), ctypes.byref(p), float(tol), int(max_iter),
                                        int(max_lanes), flags, chosen, ctx._stream()))

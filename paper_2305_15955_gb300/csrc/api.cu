@@ -82,6 +82,7 @@ cdwac_status cdwac_create(cdwac_ctx** out, int device) {
   if (const char* fl = getenv("CDWAC_FREQ_LANES")) ctx->freq_lanes = std::max(1, std::min(16, atoi(fl)));
   if (const char* la = getenv("CDWAC_LOOKAHEAD")) ctx->lookahead = atoi(la) != 0;
   if (const char* pg = getenv("CDWAC_PI_GROUP")) ctx->pi_group = std::max(1, std::min(64, atoi(pg)));
+  if (const char* pt = getenv("CDWAC_PI_TILE")) ctx->pi_tile = atoi(pt) == 128 ? 128 : 256;
   if (const char* uw = getenv("CDWAC_UPD_WAVES")) ctx->upd_waves = std::max(1, std::min(8, atoi(uw)));
   if (!create_factor_streams(ctx)) {
     cdwac_destroy(ctx);
@@ -350,6 +351,7 @@ static cdwac_status fork_lanes(cdwac_ctx* ctx, int L, cudaStream_t st) {
     ctx->lanes[l]->prof = ctx->prof;
     ctx->lanes[l]->side_stream = ctx->lookahead ? ctx->lanes[l]->own_side : nullptr;
     ctx->lanes[l]->pi_group = ctx->pi_group;
+    ctx->lanes[l]->pi_tile = ctx->pi_tile;
     ctx->lanes[l]->upd_waves = ctx->upd_waves;
     CDWAC_CUDA_TRY(ctx, cudaStreamWaitEvent(ctx->lane_streams[l], ctx->ev_fork, 0));
   }

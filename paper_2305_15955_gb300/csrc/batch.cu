@@ -6,9 +6,9 @@
 // whole batch is one stream-ordered unit that can be captured into a CUDA graph: with CDWAC_BATCH_GRAPH the first
 // call runs eagerly (sizing every lane's scratch), captures the same sequence, and later calls with identical
 // items replay the graph.  The autotuner times, per size bucket, lane counts and the lookahead switch, then the tile
-// configuration of the tensor-core kernels: the Pi tile-group size (the rasterisation of the 128 x 128 output
-// tiles over the waves) and the number of CTA waves the real trailing update's row strips are cut into (the
-// number of 128 x 32 tiles each CTA streams against its resident W digits).
+// configuration of the tensor-core kernels: the Pi output tile width (128 x 128 or 128 x 256), its tile-group size
+// (the rasterisation of the output tiles over the waves) and the number of CTA waves the real trailing update's
+// row strips are cut into (the number of 128 x 32 tiles each CTA streams against its resident W digits).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -26,6 +26,7 @@ struct Config {
   int lanes;
   int lookahead;
   int pi_group;    // Pi tile-group size (cdwac_ctx::pi_group)
+  int pi_tile;     // Pi output tile width, 128 or 256 (cdwac_ctx::pi_tile)
   int upd_waves;   // real trailing update: CTA waves of row-strip chunks (cdwac_ctx::upd_waves)
 };
 
@@ -110,6 +111,7 @@ cdwac_status enqueue(cdwac_ctx* ctx, const cdwac_batch_item* items, int n_items,
     cdwac_ctx* lane = ctx->lanes[l];
     lane->side_stream = cfg.lookahead ? lane->own_side : nullptr;
     lane->pi_group = cfg.pi_group;
+    lane->pi_tile = cfg.pi_tile;
     lane->upd_waves = cfg.upd_waves;
     lane->prof = 0;
     cudaStream_t s = ctx->lane_streams[l];
@@ -144,7 +146,7 @@ std::string bucket_of(const cdwac_batch_item* items, int n_items, const cdwac_pa
     nmax = std::max(nmax, items[i].sys.n_aux);
   }
   char buf[128];
-  snprintf(buf, sizeof(buf), "t2_n%d_c%d_a%d_p%d", n_items, (int)std::floor(std::log2(total + 1.0)),
+  snprintf(buf, sizeof(buf), "t3_n%d_c%d_a%d_p%d", n_items, (int)std::floor(std::log2(total + 1.0)),
            (int)std::floor(std::log2((double)nmax + 1.0)), prm->precision);
   return buf;
 }
@@ -155,12 +157,12 @@ bool cache_lookup(const std::string& bucket, int max_lanes, Config* cfg) {
   FILE* f = fopen(path, "r");
   if (!f) return false;
   char b[128];
-  int lanes, la, pg, uw;
+  int lanes, la, pg, pt, uw;
   double ms;
   bool found = false;
-  while (fscanf(f, "%127s %d %d %d %d %lf", b, &lanes, &la, &pg, &uw, &ms) == 6)
-    if (bucket == b && lanes <= max_lanes && pg >= 1 && pg <= 64 && uw >= 1 && uw <= 8) {
-      *cfg = {lanes, la, pg, uw};
+  while (fscanf(f, "%127s %d %d %d %d %d %lf", b, &lanes, &la, &pg, &pt, &uw, &ms) == 7)
+    if (bucket == b && lanes <= max_lanes && pg >= 1 && pg <= 64 && (pt == 128 || pt == 256) && uw >= 1 && uw <= 8) {
+      *cfg = {lanes, la, pg, pt, uw};
       found = true;
     }
   fclose(f);
@@ -172,7 +174,8 @@ void cache_store(const std::string& bucket, Config cfg, double ms) {
   if (!path) return;
   FILE* f = fopen(path, "a");
   if (!f) return;
-  fprintf(f, "%s %d %d %d %d %.3f\n", bucket.c_str(), cfg.lanes, cfg.lookahead, cfg.pi_group, cfg.upd_waves, ms);
+  fprintf(f, "%s %d %d %d %d %d %.3f\n", bucket.c_str(), cfg.lanes, cfg.lookahead, cfg.pi_group, cfg.pi_tile,
+          cfg.upd_waves, ms);
   fclose(f);
 }
 
@@ -198,7 +201,7 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
   CDWAC_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
 
-  Config cfg{std::min(max_lanes, std::min(n_items, 4)), 1, ctx->pi_group, ctx->upd_waves};
+  Config cfg{std::min(max_lanes, std::min(n_items, 4)), 1, ctx->pi_group, ctx->pi_tile, ctx->upd_waves};
   if (flags & CDWAC_BATCH_AUTOTUNE) {
     const std::string bucket = bucket_of(items, n_items, prm);
     bool have = false;
@@ -235,12 +238,19 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
       for (int lanes : {1, 2, 4, 8}) {
         if (lanes > max_lanes || lanes > n_items) continue;
         for (int la = 0; la < 2; ++la) {
-          cdwac_status rc = trial(Config{lanes, la, cfg.pi_group, cfg.upd_waves});
+          cdwac_status rc = trial(Config{lanes, la, cfg.pi_group, cfg.pi_tile, cfg.upd_waves});
           if (rc) return rc;
         }
       }
-      // stage 2: Pi tile-group size; stage 3: row-strip waves of the real trailing update (each from the best so far)
-      for (int g : {4, 8, 16}) {
+      // stage 2: Pi tile width; stage 3: Pi tile-group size; stage 4: row-strip waves of the real trailing update
+      // (each from the best so far)
+      {
+        Config c = best_cfg;
+        c.pi_tile = c.pi_tile == 128 ? 256 : 128;
+        cdwac_status rc = trial(c);
+        if (rc) return rc;
+      }
+      for (int g : {4, 8, 12, 16}) {
         Config c = best_cfg;
         if (g == c.pi_group) continue;
         c.pi_group = g;
@@ -265,7 +275,8 @@ extern "C" cdwac_status cdwac_batch_run(cdwac_ctx* ctx, const cdwac_batch_item* 
     chosen[0] = cfg.lanes;
     chosen[1] = cfg.lookahead;
     chosen[2] = cfg.pi_group;
-    chosen[3] = cfg.upd_waves;
+    chosen[3] = cfg.pi_tile;
+    chosen[4] = cfg.upd_waves;
   }
 
   if (!(flags & CDWAC_BATCH_GRAPH)) return enqueue(ctx, items, n_items, prm, tol, max_iter, cfg, st);

@@ -71,6 +71,7 @@ struct cdwac_ctx {
   bool lookahead = true;                // LDL^T bulk updates on the side stream (else one stream, no events)
   // tile configuration (chosen by the batch autotuner, or CDWAC_PI_GROUP / CDWAC_UPD_WAVES at creation):
   int pi_group = 12;                    // tensor-core Pi: tiles ordered in pi_group x pi_group groups
+  int pi_tile = 256;                    // tensor-core Pi: output tile width, 256 or 128 columns
   int upd_waves = 1;                    // real trailing update: row-strip chunks sized for this many CTA waves
   std::vector<cdwac_ctx*> lanes;
   std::vector<cudaStream_t> lane_streams;

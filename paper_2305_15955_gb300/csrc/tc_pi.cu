@@ -289,6 +289,296 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
   }
 }
 
+// ---- 128 x 256 tiles ---------------------------------------------------------------------------------------------
+// The same contraction on 128 x 256 output tiles with 32-column K-tiles (64-byte swizzle).  Each 128 x 256 x 16
+// MMA reads 4 KB of S and 8 KB of B from shared memory for twice the work of a 128 x 128 one, and a K-tile brings
+// 48 KB by TMA for 6 MMAs of 256 columns; at the tensor cores' rate per SM that is about 150 B of shared-memory
+// traffic per cycle against about 210 for the 128 x 128 kernel, whose operand reads plus TMA fills exceed the
+// shared memory's bandwidth.  Tensor memory holds one hi*hi accumulator (columns 0-255, a chain of two K-tiles,
+// four instructions, as in the 128 x 128 kernel) and one correction accumulator (columns 256-511, 64 K-tiles);
+// each K-tile issues its corrections first, so the drain reads a finished hi*hi chain while the next K-tile's
+// corrections run.  Sixteen drain warps (warps 2-17: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and the
+// 64 columns 64 ((w - 2) / 4) .. + 63) keep FP32 running sums with round-to-nearest adds.  Lower triangle: tile
+// (ti, tp) covers rows 128 ti .. + 127 and columns 256 tp .. + 255 with 2 tp <= ti; entries above the diagonal are
+// computed and not written.
+namespace w256 {
+constexpr int BM = 128, BN = 256, BK = 32;
+constexpr int SPL = BM * BK * 2;           // one S plane of a K-tile: 128 rows x 64 B = 8 KB
+constexpr int BPL = BN * BK * 2;           // one B plane of a K-tile: 256 rows x 64 B = 16 KB
+constexpr int STAGE = 2 * SPL + 2 * BPL;   // S hi, S lo, B hi, B lo: 48 KB
+constexpr int STAGES = 4;
+constexpr int SMEM = STAGES * STAGE + 1024;
+constexpr int HCH = 2;                     // K-tiles per hi*hi chain
+constexpr int CCH = 64;                    // K-tiles per correction chain
+constexpr int NT = 576;                    // warps 0 (TMA), 1 (MMA, tensor memory), 2-17 (drain)
+constexpr int NDRAIN = 16;
+constexpr uint32_t H_COL = 0, C_COL = 256;
+constexpr int LDS = BN + 1;                // staging row stride (floats)
+static_assert(BM * LDS * 4 <= STAGES * STAGE, "the staged tile fits in the operand ring");
+}  // namespace w256
+
+// Shared-memory descriptor for a K-major operand in the 64-byte swizzle layout written by TMA: rows of 64 B,
+// 8-row groups 512 B apart (stride byte offset), version 1, layout type 4 (64-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// Tile b of the lower triangle of 128 x 256 tiles: groups of G row blocks; inside a group, column pairs tp in
+// order and the group's rows ti >= 2 tp inside each.
+__device__ inline void tile256_coords(int b, int nt, int G, int& ti, int& tp) {
+  for (int r0 = 0; r0 < nt; r0 += G) {
+    const int r1 = min(nt, r0 + G);
+    for (int p = 0; 2 * p <= r1 - 1; ++p) {
+      const int first = max(r0, 2 * p), cnt = r1 - first;
+      if (cnt <= 0) continue;
+      if (b < cnt) {
+        ti = first + b;
+        tp = p;
+        return;
+      }
+      b -= cnt;
+    }
+  }
+  ti = nt;
+  tp = 0;
+}
+
+__host__ inline int tiles256(int nt) {
+  int t = 0;
+  for (int ti = 0; ti < nt; ++ti) t += ti / 2 + 1;
+  return t;
+}
+
+__device__ __forceinline__ void drain_bar512() { asm volatile("bar.sync 1, 512;" ::: "memory"); }
+// Named barrier 1 over the sixteen drain warps that also returns the AND of `v` over their threads.
+__device__ __forceinline__ bool drain_and512(bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred p, 1, 512, p;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(r)
+               : "r"((uint32_t)v)
+               : "memory");
+  return r != 0;
+}
+
+__global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_constant__ Maps maps, int n,
+                                                                int k_tiles, int group, void* A_out, int part,
+                                                                float* negpi32, unsigned* status) {
+  constexpr int BM = w256::BM, BN = w256::BN, BK = w256::BK, SPL = w256::SPL, BPL = w256::BPL;
+  constexpr int STAGE = w256::STAGE, STAGES = w256::STAGES, HCH = w256::HCH, CCH = w256::CCH;
+  constexpr int NDRAIN = w256::NDRAIN, LDS = w256::LDS;
+  constexpr uint32_t H_COL = w256::H_COL, C_COL = w256::C_COL;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t h_full, h_empty, c_full, c_empty;
+  __shared__ __align__(8) uint64_t done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+  __shared__ int issued, consumed;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nt = (n + BM - 1) / BM;
+  int ti, tp;
+  tile256_coords(blockIdx.x, nt, group, ti, tp);
+  const int row0 = ti * BM, col0 = tp * BN;
+  if (row0 >= n) return;   // past the triangle: the whole CTA leaves before any barrier or allocation
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&h_full, 1);
+    mbar_init(&c_full, 1);
+    mbar_init(&h_empty, NDRAIN);
+    mbar_init(&c_empty, NDRAIN);
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    issued = 0;
+    consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(512u)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      if (kt >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)(kt / STAGES - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], (uint32_t)STAGE);
+      uint8_t* st = smem + s * STAGE;
+      const int x = kt * BK;
+      tma_load_2d(&maps.sh, &full_bar[s], st, x, row0);
+      tma_load_2d(&maps.sl, &full_bar[s], st + SPL, x, row0);
+      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * SPL, x, col0);
+      tma_load_2d(&maps.bl, &full_bar[s], st + 2 * SPL + BPL, x, col0);
+    }
+    issued = kt;
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: corrections of K-tile kt into the correction accumulator, then its hi*hi products into the
+    // hi*hi accumulator; each chain's last K-tile commits its accumulator to the drain
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    const uint32_t dh = tmem + H_COL, dc = tmem + C_COL;
+    int kt = 0;
+    for (; kt < k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const bool c_first = kt % CCH == 0, h_first = kt % HCH == 0;
+      const bool c_last = kt % CCH == CCH - 1 || kt == k_tiles - 1;
+      const bool h_last = kt % HCH == HCH - 1 || kt == k_tiles - 1;
+      if (!mbar_wait(&full_bar[s], (uint32_t)(kt / STAGES) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      // the drain must have read the previous correction chain before a new one starts
+      if (c_first && kt > 0 && !mbar_wait(&c_empty, (uint32_t)(kt / CCH - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = smem_u32(smem + s * STAGE);
+      const uint32_t ah = base, al = base + SPL, bh = base + 2 * SPL, bl = base + 2 * SPL + BPL;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {   // 16 BF16 = 32 bytes along K inside the 64-byte swizzle row
+        const uint32_t ko = kk * 32;
+        umma(dc, sdesc64(ah + ko), sdesc64(bl + ko), idesc, (c_first && kk == 0) ? 0u : 1u);
+        umma(dc, sdesc64(al + ko), sdesc64(bh + ko), idesc, 1u);
+      }
+      if (c_last) umma_commit(&c_full);
+      // and the previous hi*hi chain before this one starts
+      if (h_first && kt > 0 && !mbar_wait(&h_empty, (uint32_t)(kt / HCH - 1) & 1u, &abort_flag)) {
+        abort_flag = 1;
+        umma_commit(&empty_bar[s]);
+        ++kt;
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk)
+        umma(dh, sdesc64(ah + kk * 32), sdesc64(bh + kk * 32), idesc, (h_first && kk == 0) ? 0u : 1u);
+      if (h_last) umma_commit(&h_full);
+      umma_commit(&empty_bar[s]);
+    }
+    consumed = kt;
+    umma_commit(&done_bar);   // arrives once every MMA issued above has completed
+  } else if (warp >= 2 && warp < 2 + NDRAIN) {
+    // ---- drain: sixteen warps; warp w reads lanes 32 (w % 4) .. + 31 and columns 64 cg .. + 63 of each chain
+    const int q = warp & 3, cg = (warp - 2) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float run[64];
+#pragma unroll
+    for (int j = 0; j < 64; ++j) run[j] = 0.f;
+    auto add_chain = [&](uint32_t col) {
+      tc_fence_after();
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {   // one 16-column load at a time: the 64 running sums leave no room for more
+        uint32_t v[16];
+        tmem_ld16_async(tmem + lane_base + col + (uint32_t)(64 * cg + 16 * c), v);
+        tmem_wait_ld16(v, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) run[16 * c + j] += __uint_as_float(v[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+    };
+    bool ok = true;
+    int hc = 0, cc = 0;
+    for (int kt = 0; kt < k_tiles && ok; ++kt) {
+      const bool c_last = kt % CCH == CCH - 1 || kt == k_tiles - 1;
+      const bool h_last = kt % HCH == HCH - 1 || kt == k_tiles - 1;
+      if (c_last) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&c_full, (uint32_t)cc & 1u, &abort_flag));
+        if (!ok) break;
+        add_chain(C_COL);
+        if (lane == 0) mbar_arrive(&c_empty);
+        ++cc;
+      }
+      if (h_last) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&h_full, (uint32_t)hc & 1u, &abort_flag));
+        if (!ok) break;
+        add_chain(H_COL);
+        if (lane == 0) mbar_arrive(&h_empty);
+        ++hc;
+      }
+    }
+    if (!ok) abort_flag = 1;
+    // every drain warp is done (a timeout in one ends the others' bounded waits too); the verdict is the AND over
+    // the sixteen warps, the same in all of them, so the barriers below are reached by all or none
+    if (drain_and512(ok && !abort_flag)) {
+      // the last chain's commit follows every MMA, so the operand ring is free: stage the tile (row stride
+      // BN + 1 floats) and write it out as coalesced row segments
+      float* stg = reinterpret_cast<float*>(smem);
+#pragma unroll
+      for (int j = 0; j < 64; ++j) stg[(q * 32 + lane) * LDS + 64 * cg + j] = run[j];
+      drain_bar512();
+      const int e = warp - 2;   // rows 8 e .. 8 e + 7 of the tile
+      for (int rr = 0; rr < 8; ++rr) {
+        const int row = row0 + 8 * e + rr;
+        if (row >= n) break;
+        const float* src = stg + (8 * e + rr) * LDS;
+        for (int j = lane; j < BN; j += 32) {
+          const int col = col0 + j;
+          if (col > row || col >= n) continue;
+          const double diag = col == row ? 1.0 : 0.0;
+          if (part < 0) {
+            reinterpret_cast<double*>(A_out)[(long)row * n + col] = diag + (double)src[j];
+            if (negpi32) negpi32[(long)row * n + col] = src[j];   // -Pi in FP32 for the Pi O product
+          } else {
+            double* Ac = reinterpret_cast<double*>(A_out) + 2 * ((long)row * n + col) + part;
+            *Ac = (part == 0 ? diag : 0.0) + (double)src[j];
+          }
+        }
+      }
+      if (part < 0 && negpi32) {
+        // the transposed (upper) entries: the 32 lanes hold consecutive rows, so every store is coalesced
+        const int row = row0 + q * 32 + lane;
+        for (int j = 64 * cg; j < 64 * cg + 64; ++j) {
+          const int col = col0 + j;
+          if (row < n && col < row) negpi32[(long)col * n + row] = stg[(q * 32 + lane) * LDS + j];
+        }
+      }
+    }
+  }
+  __syncwarp();
+
+  // every MMA issued has completed before the tensor memory is released, on every path
+  const bool done_ok = mbar_wait(&done_bar, 0, nullptr);
+  tc_fence_after();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!done_ok || abort_flag) {
+      raise_status(status, DEV_ERR_TIMEOUT);
+      for (int kt = consumed; kt < issued; ++kt)
+        mbar_wait(&full_bar[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, nullptr);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+  }
+}
+
 // ---- operand preparation (HBM-bound elementwise passes) ---------------------------------------------------------
 
 __device__ __forceinline__ void split8(const float (&v)[8], uint4& hi, uint4& lo) {
@@ -424,9 +714,41 @@ int elementwise_blocks(cdwac_ctx* ctx, long work) {
   return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
 }
 
-// One launch of the contraction with the weighted planes (sh, sl): part as in tc_syrk_kernel.
+// TMA map of a plane for the 128 x 256 kernel: 32-column boxes, 64-byte swizzle.
+bool make_map64(CUtensorMap* m, const void* base, int rows, long kpad, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kpad * 2};
+  cuuint32_t box[2] = {(cuuint32_t)w256::BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cdwac_status run_syrk256(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl, int n,
+                         void* A, int part, float* negpi32, cudaStream_t st) {
+  Maps maps;
+  memset(&maps, 0, sizeof(maps));
+  if (!make_map64(&maps.sh, sh, n, s.kpad, w256::BM) || !make_map64(&maps.sl, sl, n, s.kpad, w256::BM) ||
+      !make_map64(&maps.bh, s.bh, n, s.kpad, w256::BN) || !make_map64(&maps.bl, s.bl, n, s.kpad, w256::BN))
+    return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
+  CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           w256::SMEM));
+  const int nt = (n + w256::BM - 1) / w256::BM;
+  const int group = ctx->pi_group >= 1 && ctx->pi_group <= 64 ? ctx->pi_group : 12;
+  tc_syrk256_kernel<<<tiles256(nt), w256::NT, w256::SMEM, st>>>(maps, n, (int)(s.kpad / w256::BK), group, A, part,
+                                                                negpi32, ctx->d_status);
+  CDWAC_LAUNCH_CHECK(ctx);
+  return CDWAC_OK;
+}
+
+// One launch of the contraction with the weighted planes (sh, sl): part as in tc_syrk_kernel; 128 x 256 tiles
+// (the context's pi_tile, 256 by default) or 128 x 128 tiles.
 cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl, int n,
                       void* A, int part, float* negpi32, cudaStream_t st) {
+  if (ctx->pi_tile != 128) return run_syrk256(ctx, s, sh, sl, n, A, part, negpi32, st);
   Maps maps;
   memset(&maps, 0, sizeof(maps));
   if (!make_map(&maps.sh, sh, n, s.kpad) || !make_map(&maps.sl, sl, n, s.kpad) || !make_map(&maps.bh, s.bh, n, s.kpad) ||

@@ -45,14 +45,22 @@ def test_batch_matches_single_system_calls(precision, tmp_path, monkeypatch):
     ctx = cdwac.Context(0)
     res = [cdwac.BatchResult(s, p, omega, omega, dev) for s in systems]
     chosen, items = cdwac.batch_run(ctx, res, p, max_lanes=4, autotune=True)
-    # lanes, lookahead, then the tile configuration: Pi tile-group size and the real update's strip waves
-    assert 1 <= chosen[0] <= 4 and chosen[1] in (0, 1) and chosen[2] in (4, 8, 12, 16) and chosen[3] in (1, 2, 3)
+    # lanes, lookahead, then the tile configuration: Pi tile-group size and width, the real update's strip waves
+    assert 1 <= chosen[0] <= 4 and chosen[1] in (0, 1) and chosen[2] in (4, 8, 12, 16)
+    assert chosen[3] in (128, 256) and chosen[4] in (1, 2, 3)
     # the cache holds the whole choice, and a second call with the same bucket reads it back
     line = (tmp_path / "tune.txt").read_text().split()
-    assert [int(x) for x in line[1:5]] == list(chosen)
+    assert [int(x) for x in line[1:6]] == list(chosen)
     again, _ = cdwac.batch_run(ctx, res, p, max_lanes=4, autotune=True)
     assert again == chosen
     assert (tmp_path / "tune.txt").exists()
+    ctx.close()
+    # the single-system calls in the tile configuration the batch chose (the two Pi tile widths round their
+    # 2048-column chunk sums in a different order)
+    monkeypatch.setenv("CDWAC_PI_GROUP", str(chosen[2]))
+    monkeypatch.setenv("CDWAC_PI_TILE", str(chosen[3]))
+    monkeypatch.setenv("CDWAC_UPD_WAVES", str(chosen[4]))
+    ctx = cdwac.Context(0)
     for s, r in zip(systems, res):
         xi, wxi, W = ctx.build_W_imag(s, p)
         pade = ctx.fit_pade(s, p, xi, W)
