@@ -294,13 +294,19 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
 // MMA reads 4 KB of S and 8 KB of B from shared memory for twice the work of a 128 x 128 one, and a K-tile brings
 // 48 KB by TMA for 6 MMAs of 256 columns; at the tensor cores' rate per SM that is about 150 B of shared-memory
 // traffic per cycle against about 210 for the 128 x 128 kernel, whose operand reads plus TMA fills exceed the
-// shared memory's bandwidth.  Tensor memory holds one hi*hi accumulator (columns 0-255, a chain of two K-tiles,
-// four instructions, as in the 128 x 128 kernel) and one correction accumulator (columns 256-511, 64 K-tiles);
-// each K-tile issues its corrections first, so the drain reads a finished hi*hi chain while the next K-tile's
-// corrections run.  Sixteen drain warps (warps 2-17: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and the
-// 64 columns 64 ((w - 2) / 4) .. + 63) keep FP32 running sums with round-to-nearest adds.  Lower triangle: tile
-// (ti, tp) covers rows 128 ti .. + 127 and columns 256 tp .. + 255 with 2 tp <= ti; entries above the diagonal are
-// computed and not written.
+// shared memory's bandwidth.
+// Accumulation: every two K-tiles form one chain of twelve instructions in a fresh 256-column tensor-memory
+// accumulator, two accumulators in turn (all 512 columns); each K-tile issues its hi*lo and lo*hi corrections
+// first and its two hi*hi products last.  The tensor cores' accumulation loses a fraction of an ulp of the
+// accumulator towards zero per instruction; in this order a chain's bias stays near 4.5 x 2^-25 of its value
+// (1.3e-7; chains of one K-tile's four hi*hi instructions: 2.5 x 2^-25), and the acene-like core QP energy moves
+// by 0.03 meV (0.20 -> 0.23 meV from the FP64 oracle, W(i xi) within 5.4e-7).
+// Sixteen drain warps (warps 2-17: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 and the 64 columns
+// 64 ((w - 2) / 4) .. + 63) add each finished chain into FP32 running sums with round-to-nearest adds while the
+// MMAs fill the other accumulator: a drain has two K-tiles (12 MMAs) of time, where a single hi*hi accumulator
+// beside a correction accumulator left it the four correction MMAs of one K-tile and stalled the tensor cores.  Lower triangle:
+// tile (ti, tp) covers rows 128 ti .. + 127 and columns 256 tp .. + 255 with 2 tp <= ti; entries above the
+// diagonal are computed and not written.
 namespace w256 {
 constexpr int BM = 128, BN = 256, BK = 32;
 constexpr int SPL = BM * BK * 2;           // one S plane of a K-tile: 128 rows x 64 B = 8 KB
@@ -308,11 +314,8 @@ constexpr int BPL = BN * BK * 2;           // one B plane of a K-tile: 256 rows 
 constexpr int STAGE = 2 * SPL + 2 * BPL;   // S hi, S lo, B hi, B lo: 48 KB
 constexpr int STAGES = 4;
 constexpr int SMEM = STAGES * STAGE + 1024;
-constexpr int HCH = 2;                     // K-tiles per hi*hi chain
-constexpr int CCH = 64;                    // K-tiles per correction chain
 constexpr int NT = 576;                    // warps 0 (TMA), 1 (MMA, tensor memory), 2-17 (drain)
 constexpr int NDRAIN = 16;
-constexpr uint32_t H_COL = 0, C_COL = 256;
 constexpr int LDS = BN + 1;                // staging row stride (floats)
 static_assert(BM * LDS * 4 <= STAGES * STAGE, "the staged tile fits in the operand ring");
 }  // namespace w256
@@ -366,18 +369,15 @@ __device__ __forceinline__ bool drain_and512(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_constant__ Maps maps, int n,
-                                                                int k_tiles, int group, void* A_out, int part,
-                                                                float* negpi32, unsigned* status) {
+__global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_constant__ Maps maps, int n, int k_tiles, int group,
+                                                    void* A_out, int part, float* negpi32, unsigned* status) {
   constexpr int BM = w256::BM, BN = w256::BN, BK = w256::BK, SPL = w256::SPL, BPL = w256::BPL;
-  constexpr int STAGE = w256::STAGE, STAGES = w256::STAGES, HCH = w256::HCH, CCH = w256::CCH;
-  constexpr int NDRAIN = w256::NDRAIN, LDS = w256::LDS;
-  constexpr uint32_t H_COL = w256::H_COL, C_COL = w256::C_COL;
+  constexpr int STAGE = w256::STAGE, STAGES = w256::STAGES, NDRAIN = w256::NDRAIN, LDS = w256::LDS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t h_full, h_empty, c_full, c_empty;
+  __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
   __shared__ __align__(8) uint64_t done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int abort_flag;
@@ -395,10 +395,10 @@ __global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_co
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&h_full, 1);
-    mbar_init(&c_full, 1);
-    mbar_init(&h_empty, NDRAIN);
-    mbar_init(&c_empty, NDRAIN);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], NDRAIN);
+    }
     mbar_init(&done_bar, 1);
     abort_flag = 0;
     issued = 0;
@@ -435,47 +435,34 @@ __global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_co
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer: corrections of K-tile kt into the correction accumulator, then its hi*hi products into the
-    // hi*hi accumulator; each chain's last K-tile commits its accumulator to the drain
+    // ---- MMA issuer: K-tiles 2c and 2c + 1 form chain c in accumulator c % 2 (columns 256 (c % 2) ..)
     constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    const uint32_t dh = tmem + H_COL, dc = tmem + C_COL;
     int kt = 0;
     for (; kt < k_tiles; ++kt) {
-      const int s = kt % STAGES;
-      const bool c_first = kt % CCH == 0, h_first = kt % HCH == 0;
-      const bool c_last = kt % CCH == CCH - 1 || kt == k_tiles - 1;
-      const bool h_last = kt % HCH == HCH - 1 || kt == k_tiles - 1;
+      const int s = kt % STAGES, c = kt >> 1, ab = c & 1;
+      const bool c_first = (kt & 1) == 0, c_last = (kt & 1) == 1 || kt == k_tiles - 1;
       if (!mbar_wait(&full_bar[s], (uint32_t)(kt / STAGES) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
-      // the drain must have read the previous correction chain before a new one starts
-      if (c_first && kt > 0 && !mbar_wait(&c_empty, (uint32_t)(kt / CCH - 1) & 1u, &abort_flag)) {
+      // the drain must have read this accumulator's previous chain (chain c - 2)
+      if (c_first && c >= 2 && !mbar_wait(&acc_empty[ab], (uint32_t)(c / 2 - 1) & 1u, &abort_flag)) {
         abort_flag = 1;
         break;
       }
       tc_fence_after();
       const uint32_t base = smem_u32(smem + s * STAGE);
       const uint32_t ah = base, al = base + SPL, bh = base + 2 * SPL, bl = base + 2 * SPL + BPL;
+      const uint32_t d = tmem + (uint32_t)(256 * ab);
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {   // 16 BF16 = 32 bytes along K inside the 64-byte swizzle row
         const uint32_t ko = kk * 32;
-        umma(dc, sdesc64(ah + ko), sdesc64(bl + ko), idesc, (c_first && kk == 0) ? 0u : 1u);
-        umma(dc, sdesc64(al + ko), sdesc64(bh + ko), idesc, 1u);
+        umma(d, sdesc64(ah + ko), sdesc64(bl + ko), idesc, (c_first && kk == 0) ? 0u : 1u);
+        umma(d, sdesc64(al + ko), sdesc64(bh + ko), idesc, 1u);
       }
-      if (c_last) umma_commit(&c_full);
-      // and the previous hi*hi chain before this one starts
-      if (h_first && kt > 0 && !mbar_wait(&h_empty, (uint32_t)(kt / HCH - 1) & 1u, &abort_flag)) {
-        abort_flag = 1;
-        umma_commit(&empty_bar[s]);
-        ++kt;
-        break;
-      }
-      tc_fence_after();
 #pragma unroll
-      for (int kk = 0; kk < BK / 16; ++kk)
-        umma(dh, sdesc64(ah + kk * 32), sdesc64(bh + kk * 32), idesc, (h_first && kk == 0) ? 0u : 1u);
-      if (h_last) umma_commit(&h_full);
+      for (int kk = 0; kk < BK / 16; ++kk) umma(d, sdesc64(ah + kk * 32), sdesc64(bh + kk * 32), idesc, 1u);
+      if (c_last) umma_commit(&acc_full[ab]);
       umma_commit(&empty_bar[s]);
     }
     consumed = kt;
@@ -487,38 +474,25 @@ __global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_co
     float run[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) run[j] = 0.f;
-    auto add_chain = [&](uint32_t col) {
+    bool ok = true;
+    const int n_chains = (k_tiles + 1) / 2;
+    for (int c = 0; c < n_chains; ++c) {
+      const int ab = c & 1;
+      // accumulator ab's next phase needs this drain's arrival first, so the phase cannot pass unobserved
+      ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[ab], (uint32_t)(c / 2) & 1u, &abort_flag));
+      if (!ok) break;
       tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {   // one 16-column load at a time: the 64 running sums leave no room for more
+      for (int i = 0; i < 4; ++i) {   // one 16-column load at a time: the 64 running sums leave no room for more
         uint32_t v[16];
-        tmem_ld16_async(tmem + lane_base + col + (uint32_t)(64 * cg + 16 * c), v);
+        tmem_ld16_async(tmem + lane_base + (uint32_t)(256 * ab + 64 * cg + 16 * i), v);
         tmem_wait_ld16(v, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) run[16 * c + j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 16; ++j) run[16 * i + j] += __uint_as_float(v[j]);
       }
       tc_fence_before();
       __syncwarp();
-    };
-    bool ok = true;
-    int hc = 0, cc = 0;
-    for (int kt = 0; kt < k_tiles && ok; ++kt) {
-      const bool c_last = kt % CCH == CCH - 1 || kt == k_tiles - 1;
-      const bool h_last = kt % HCH == HCH - 1 || kt == k_tiles - 1;
-      if (c_last) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&c_full, (uint32_t)cc & 1u, &abort_flag));
-        if (!ok) break;
-        add_chain(C_COL);
-        if (lane == 0) mbar_arrive(&c_empty);
-        ++cc;
-      }
-      if (h_last) {
-        ok = __all_sync(0xffffffffu, mbar_wait(&h_full, (uint32_t)hc & 1u, &abort_flag));
-        if (!ok) break;
-        add_chain(H_COL);
-        if (lane == 0) mbar_arrive(&h_empty);
-        ++hc;
-      }
+      if (lane == 0) mbar_arrive(&acc_empty[ab]);
     }
     if (!ok) abort_flag = 1;
     // every drain warp is done (a timeout in one ends the others' bounded waits too); the verdict is the AND over

@@ -90,10 +90,11 @@ def test_mixed_plain_cd_sigma(ctx):
 
 
 def test_pi_tile_widths_agree(monkeypatch):
-    """The 128 x 256 and 128 x 128 tensor-core Pi kernels sum the same split-BF16 products in the same chunks
-    (hi*hi chains of 64 columns, corrections of 2048) and differ only in the order of two round-to-nearest FP32
-    adds at each 2048-column boundary: W(i xi) and W(z) from the two agree far inside the mixed tolerance
-    (N_aux = 300: two 128 x 256 column pairs, a ragged last row block of 44 rows)."""
+    """The 128 x 256 and 128 x 128 tensor-core Pi kernels sum the same split-BF16 products and differ only in how
+    the FP32 accumulation is chunked (128 x 256: corrections and hi*hi products of 64 columns per chain; 128 x 128:
+    hi*hi per 64 columns, corrections per 2048), i.e. in FP32 rounding: W(i xi) and W(z) from the two agree far
+    inside the mixed path's 2^-15 error model (N_aux = 300: two 128 x 256 column pairs, a ragged last row block
+    of 44 rows)."""
     spec = inputs.custom_system(96, 9, 300, seed=23, n_core=2, states=(0, 1))
     eps = inputs.eigenvalues(spec)
     sysd = cdwac.System(eps, inputs.build_B(spec, dtype=np.float32), inputs.build_On(spec, dtype=np.float32),
@@ -109,7 +110,7 @@ def test_pi_tile_widths_agree(monkeypatch):
             out[width] = (W.cpu().numpy(), pade.W_real.cpu().numpy())
         finally:
             c.close()
-    # FP32 rounding of Pi (relative ~6e-8) reaches W through cond(I - Pi): about 10 on the imaginary axis, up to
+    # FP32 rounding of Pi (relative ~1e-7) reaches W through cond(I - Pi): about 10 on the imaginary axis, up to
     # ~1e4 at the near-real points (Im z = 1e-3 Ha)
-    for (a, b), tol in zip(zip(out[128], out[256]), (1e-6, 1e-3)):
+    for (a, b), tol in zip(zip(out[128], out[256]), (1e-5, 1e-3)):
         assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(a)), np.max(np.abs(a - b)) / np.max(np.abs(a))
