@@ -369,8 +369,12 @@ __device__ __forceinline__ bool drain_and512(bool v) {
   return r != 0;
 }
 
-__global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_constant__ Maps maps, int n, int k_tiles, int group,
-                                                    void* A_out, int part, float* negpi32, unsigned* status) {
+// part >= 0 (complex A): blocks [0, tiles) write the real parts with the weighted planes of `maps`, blocks
+// [tiles, 2 tiles) the imaginary parts with those of `maps_im` (one launch for both contractions).
+__global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_constant__ Maps maps,
+                                                                const __grid_constant__ Maps maps_im, int tiles,
+                                                                int n, int k_tiles, int group, void* A_out, int part,
+                                                                float* negpi32, unsigned* status) {
   constexpr int BM = w256::BM, BN = w256::BN, BK = w256::BK, SPL = w256::SPL, BPL = w256::BPL;
   constexpr int STAGE = w256::STAGE, STAGES = w256::STAGES, NDRAIN = w256::NDRAIN, LDS = w256::LDS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -385,8 +389,11 @@ __global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_co
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nt = (n + BM - 1) / BM;
+  const bool second = part >= 0 && (int)blockIdx.x >= tiles;
+  if (part >= 0) part = second ? 1 : 0;
+  const Maps* mp = second ? &maps_im : &maps;
   int ti, tp;
-  tile256_coords(blockIdx.x, nt, group, ti, tp);
+  tile256_coords(second ? (int)blockIdx.x - tiles : (int)blockIdx.x, nt, group, ti, tp);
   const int row0 = ti * BM, col0 = tp * BN;
   if (row0 >= n) return;   // past the triangle: the whole CTA leaves before any barrier or allocation
 
@@ -428,10 +435,10 @@ __global__ void __launch_bounds__(w256::NT, 1) tc_syrk256_kernel(const __grid_co
       mbar_expect_tx(&full_bar[s], (uint32_t)STAGE);
       uint8_t* st = smem + s * STAGE;
       const int x = kt * BK;
-      tma_load_2d(&maps.sh, &full_bar[s], st, x, row0);
-      tma_load_2d(&maps.sl, &full_bar[s], st + SPL, x, row0);
-      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * SPL, x, col0);
-      tma_load_2d(&maps.bl, &full_bar[s], st + 2 * SPL + BPL, x, col0);
+      tma_load_2d(&mp->sh, &full_bar[s], st, x, row0);
+      tma_load_2d(&mp->sl, &full_bar[s], st + SPL, x, row0);
+      tma_load_2d(&mp->bh, &full_bar[s], st + 2 * SPL, x, col0);
+      tma_load_2d(&mp->bl, &full_bar[s], st + 2 * SPL + BPL, x, col0);
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
@@ -701,19 +708,26 @@ bool make_map64(CUtensorMap* m, const void* base, int rows, long kpad, int box_r
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-cdwac_status run_syrk256(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl, int n,
-                         void* A, int part, float* negpi32, cudaStream_t st) {
-  Maps maps;
+// One launch on 128 x 256 tiles: part < 0 the real A with the weighted planes (sh, sl); part >= 0 both parts of
+// the complex A, the real parts with (sh, sl) and the imaginary parts with (sh2, sl2).
+cdwac_status run_syrk256(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl,
+                         const __nv_bfloat16* sh2, const __nv_bfloat16* sl2, int n, void* A, int part, float* negpi32,
+                         cudaStream_t st) {
+  Maps maps, maps_im;
   memset(&maps, 0, sizeof(maps));
   if (!make_map64(&maps.sh, sh, n, s.kpad, w256::BM) || !make_map64(&maps.sl, sl, n, s.kpad, w256::BM) ||
       !make_map64(&maps.bh, s.bh, n, s.kpad, w256::BN) || !make_map64(&maps.bl, s.bl, n, s.kpad, w256::BN))
     return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
+  maps_im = maps;
+  if (part >= 0 && (!make_map64(&maps_im.sh, sh2, n, s.kpad, w256::BM) ||
+                    !make_map64(&maps_im.sl, sl2, n, s.kpad, w256::BM)))
+    return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed (n=%d kpad=%ld)", n, s.kpad);
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_syrk256_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            w256::SMEM));
-  const int nt = (n + w256::BM - 1) / w256::BM;
+  const int nt = (n + w256::BM - 1) / w256::BM, tiles = tiles256(nt);
   const int group = ctx->pi_group >= 1 && ctx->pi_group <= 64 ? ctx->pi_group : 12;
-  tc_syrk256_kernel<<<tiles256(nt), w256::NT, w256::SMEM, st>>>(maps, n, (int)(s.kpad / w256::BK), group, A, part,
-                                                                negpi32, ctx->d_status);
+  tc_syrk256_kernel<<<part >= 0 ? 2 * tiles : tiles, w256::NT, w256::SMEM, st>>>(
+      maps, maps_im, tiles, n, (int)(s.kpad / w256::BK), group, A, part, negpi32, ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
 }
@@ -722,7 +736,7 @@ cdwac_status run_syrk256(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* 
 // (the context's pi_tile, 256 by default) or 128 x 128 tiles.
 cdwac_status run_syrk(cdwac_ctx* ctx, const Scratch& s, const __nv_bfloat16* sh, const __nv_bfloat16* sl, int n,
                       void* A, int part, float* negpi32, cudaStream_t st) {
-  if (ctx->pi_tile != 128) return run_syrk256(ctx, s, sh, sl, n, A, part, negpi32, st);
+  if (ctx->pi_tile != 128) return run_syrk256(ctx, s, sh, sl, nullptr, nullptr, n, A, part, negpi32, st);
   Maps maps;
   memset(&maps, 0, sizeof(maps));
   if (!make_map(&maps.sh, sh, n, s.kpad) || !make_map(&maps.sl, sl, n, s.kpad) || !make_map(&maps.bh, s.bh, n, s.kpad) ||
@@ -817,7 +831,8 @@ cdwac_status tc_pi_complex(cdwac_ctx* ctx, const void* shared, void* lane, const
   }
   if (rc) return rc;
   ProfScope ps(ctx, PROF_PI_TC_CPLX, st);
-  // real and imaginary parts as two real contractions sharing the B planes
+  // real and imaginary parts as two real contractions sharing the B planes (one launch on 128 x 256 tiles)
+  if (ctx->pi_tile != 128) return run_syrk256(ctx, s, s.s0h, s.s0l, s.s1h, s.s1l, n_aux, A, 0, nullptr, st);
   if ((rc = run_syrk(ctx, s, s.s0h, s.s0l, n_aux, A, 0, nullptr, st))) return rc;
   return run_syrk(ctx, s, s.s1h, s.s1l, n_aux, A, 1, nullptr, st);
 }
