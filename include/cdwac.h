@@ -28,9 +28,12 @@
  *     lanes, the factorisation's critical-path and side streams) and joins them back before it returns.
  *   - Tuning read once when a context is created: CDWAC_FREQ_LANES (concurrent frequency lanes of a W build,
  *     1..16, default 8, further limited to half of the free device memory), CDWAC_LOOKAHEAD (0 runs the
- *     factorisation's bulk updates in line instead of on a side stream; default 1).  A process that runs the
- *     default eight lanes does best with CUDA_DEVICE_MAX_CONNECTIONS=32 set before CUDA initialises (bench.py
- *     does so).
+ *     factorisation's bulk updates in line instead of on a side stream; default 1), CDWAC_PI_TILE (width of the
+ *     tensor-core Pi tiles, 256 or 128; default 256), CDWAC_PI_GROUP (row blocks per group in the order of the Pi
+ *     tiles, 1..64; default 12) and CDWAC_UPD_WAVES (CTA waves of the real trailing update's row-strip chunks,
+ *     1..8; default 1); none of the last three changes a result beyond FP32 rounding in Pi.  A process that runs
+ *     the default eight lanes does best with CUDA_DEVICE_MAX_CONNECTIONS=32 set before CUDA initialises
+ *     (bench.py does so).
  */
 #ifndef CDWAC_H
 #define CDWAC_H

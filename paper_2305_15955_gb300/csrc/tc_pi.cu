@@ -228,8 +228,9 @@ __global__ void __launch_bounds__(384, 1) tc_syrk_kernel(const __grid_constant__
       if (kt % CORR == CORR - 1 || kt == k_tiles - 1) drain(&cr_empty, NHH);
     }
     if (!ok) abort_flag = 1;
-    drain_bar();   // every drain warp is done (a timeout in one ends the others' bounded waits too)
-    if (!abort_flag) {
+    // every drain warp is done (a timeout in one ends the others' bounded waits too); the verdict is the AND over
+    // the eight drain warps, the same in all of them, so the barrier below is reached by all or none
+    if (drain_and256(ok && !abort_flag)) {
       // The last drain means every MMA has completed and every operand stage has been consumed, so the operand
       // ring is free: the tile is staged there (row stride BN + 1 floats: conflict-free both ways) and written
       // out as coalesced row segments, this warp's 32 rows and its group's 64 columns.

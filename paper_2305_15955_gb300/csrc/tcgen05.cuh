@@ -153,6 +153,15 @@ __device__ __forceinline__ void tmem_add64(uint32_t taddr, float (&run)[64]) {
 }
 // Named barrier 1 over the two drain warpgroups (warps 4-11).
 __device__ __forceinline__ void drain_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The same barrier, returning the AND of `v` over the 256 threads (a decision every drain warp then shares).
+__device__ __forceinline__ bool drain_and256(bool v) {
+  uint32_t r;
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred p, 1, 256, p;\n selp.u32 %0, 1, 0, p;\n}\n"
+               : "=r"(r)
+               : "r"((uint32_t)v)
+               : "memory");
+  return r != 0;
+}
 
 // 3-D TMA tile load (x = innermost element, y = row, z = plane).
 __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
