@@ -9,6 +9,10 @@
 //   for b:  Y_b = L_bb^-1 T_b                   CUDA cores, FP32 (64 x 64 times 64 x 2C), W partial sums in FP64
 //           T_>b -= L_>b,b Y_b                  split-BF16 tensor-core GEMM with K = 64
 //
+// The updates are grouped by eight blocks (512 rows): inside a group each step updates only the group's remaining
+// rows, and after a group's last block one GEMM with K = 512 updates every row below it, so the FP32 right-hand
+// sides below a group are read and written once per group instead of once per block.
+//
 // Near the real axis (complex symmetric L, real o) the same blocked substitution gives y = L^-1 o and
 // W_nm = sum_P y_P^2 / d_P - sum_P o_P^2 (W is O(1) there: no cancellation).  The complex update is one real GEMM
 // with K = 128 per block: A = [Re L | -Im L], and the rows of B are [Re y | Im y] for the real parts of T and
@@ -16,11 +20,14 @@
 //
 // T is held column-major (T[col][row], col < 2C) so that both the GEMM epilogue (a warp writes 32 consecutive rows
 // of one column) and the block solve (64 consecutive rows of a column) touch contiguous memory.  The BF16 planes of
-// the factor, of Pi and of O^T are K-major for TMA (128-byte swizzle); the planes of Y_b are [2C][64].  The
+// the factor, of Pi and of O^T are K-major for TMA (128-byte swizzle); the planes of a group's Y_b are [2C][512]
+// (complex [2C][1024]).  The
 // products carry ~2^-16 relative error per term like the tensor-core Pi, which dominates the mixed path's error.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <string.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "tcgen05.cuh"
@@ -36,12 +43,13 @@ constexpr int SMEM = STAGES * STAGE + 1024;
 constexpr int NHH = STAGES;        // hi*hi accumulator buffers, one per operand stage (see tc_gemm_kernel)
 constexpr int CORR = 32;           // K-tiles per correction accumulator (one buffer)
 constexpr int TMEM_COLS = 4 * BN;  // three hi*hi buffers and the corrections
+constexpr int GB = 8;              // 64-row blocks per group of the blocked substitution's updates
 
 struct GemmMaps {
   CUtensorMap ah, al, bh, bl;
 };
 
-// out[(col) * ld + row_off + row] (=, -=) sum_k A[a_y0 + row][a_x0 + k] B[b_y0 + col][k],  row < M, col < N.
+// out[(col) * ld + row_off + row] (=, -=) sum_k A[a_y0 + row][a_x0 + k] B[b_y0 + col][b_x0 + k], row < M, col < N.
 // The tensor cores' FP32 accumulation loses a fraction of an ulp towards zero at every instruction, a bias over
 // long chains (the Pi O product runs over K = N_aux), so the hi*hi products of every K-tile go to a fresh
 // accumulator (three in turn) and the hi*lo + lo*hi corrections to one refreshed every CORR K-tiles, and warps 4-11 (two warpgroups, half the columns each) add every finished accumulator into FP32
@@ -49,8 +57,8 @@ struct GemmMaps {
 // issues the MMAs, warps 2-3 are idle.
 template <bool SUB>
 __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__ GemmMaps maps, int M, int N,
-                                                         int k_tiles, int a_x0, int a_y0, int b_y0, float* out,
-                                                         long ld, int row_off, unsigned* status) {
+                                                         int k_tiles, int a_x0, int a_y0, int b_x0, int b_y0,
+                                                         float* out, long ld, int row_off, unsigned* status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
@@ -102,8 +110,8 @@ __global__ void __launch_bounds__(384, 1) tc_gemm_kernel(const __grid_constant__
       const int x = a_x0 + kt * BK;
       tma_load_2d(&maps.ah, &full_bar[s], st + 0 * PLANE, x, a_y0 + tm * BM);
       tma_load_2d(&maps.al, &full_bar[s], st + 1 * PLANE, x, a_y0 + tm * BM);
-      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * PLANE, kt * BK, b_y0 + tn * BN);
-      tma_load_2d(&maps.bl, &full_bar[s], st + 3 * PLANE, kt * BK, b_y0 + tn * BN);
+      tma_load_2d(&maps.bh, &full_bar[s], st + 2 * PLANE, b_x0 + kt * BK, b_y0 + tn * BN);
+      tma_load_2d(&maps.bl, &full_bar[s], st + 3 * PLANE, b_x0 + kt * BK, b_y0 + tn * BN);
     }
     issued = kt;
   } else if (warp == 1 && lane == 0) {
@@ -281,15 +289,16 @@ __global__ void o_transpose_kernel(const TIn* __restrict__ O, long o_state_strid
   }
 }
 
-// Block step b: Y_b = X_b T_b for every column (X_b = L_bb^-1, unit lower), written as BF16 hi/lo planes
-// [2C][64] for the next update, and the W partial sums  part[b][m] = sum_r y[m][r] y[C + m][r] / d_r.
+// Block step b: Y_b = X_b T_b for every column (X_b = L_bb^-1, unit lower), written as BF16 hi/lo planes into
+// columns yo .. yo + 63 of [2C][ys] for the updates, and the W partial sums  part[b][m] = sum_r y[m][r] y[C + m][r]
+// / d_r.
 // One CTA per 16 column pairs (m, C + m); thread (r, g) owns row r and columns {4 of m, their 4 partners}.
 constexpr int SP = 16;
 __global__ void __launch_bounds__(256) block_solve_kernel(const float* __restrict__ T, long ld, int n, int C, int b,
                                                           const float* __restrict__ linv32,
                                                           const double* __restrict__ dinv,
                                                           __nv_bfloat16* __restrict__ yh,
-                                                          __nv_bfloat16* __restrict__ yl,
+                                                          __nv_bfloat16* __restrict__ yl, int ys, int yo,
                                                           double* __restrict__ part) {
   __shared__ float Xs[64][65];
   __shared__ float Ts[2 * SP][65];
@@ -331,11 +340,11 @@ __global__ void __launch_bounds__(256) block_solve_kernel(const float* __restric
     if (m < C) {
       __nv_bfloat16 h, l;
       split_bf16(y[j], h, l);
-      yh[(long)m * 64 + r] = h;
-      yl[(long)m * 64 + r] = l;
+      yh[(long)m * ys + yo + r] = h;
+      yl[(long)m * ys + yo + r] = l;
       split_bf16(y[4 + j], h, l);
-      yh[(long)(C + m) * 64 + r] = h;
-      yl[(long)(C + m) * 64 + r] = l;
+      yh[(long)(C + m) * ys + yo + r] = h;
+      yl[(long)(C + m) * ys + yo + r] = l;
     }
   }
   __syncthreads();
@@ -386,15 +395,16 @@ __global__ void cfactor_split_kernel(const cplx* __restrict__ L, int n, int npad
   }
 }
 
-// Block step b, complex: Y_b = X_b T_b (T rows c = Re, C + c = Im), planes [2C][128] for the update
-// (row c: [Re y | Im y], row C + c: [Im y | -Re y]) and part[b][c] = sum_r y_r^2 / d_r (complex, FP64).
+// Block step b, complex: Y_b = X_b T_b (T rows c = Re, C + c = Im), planes in columns yo .. yo + 127 of [2C][ys]
+// for the updates (row c: [Re y | Im y], row C + c: [Im y | -Re y]) and part[b][c] = sum_r y_r^2 / d_r (complex,
+// FP64).
 // One CTA per 8 columns; thread (r, g) owns row r of columns 2g and 2g + 1.
 constexpr int SPC = 8;
 __global__ void __launch_bounds__(256) block_solve_c_kernel(const float* __restrict__ T, long ld, int n, int C, int b,
                                                             const f2* __restrict__ linv32,
                                                             const cplx* __restrict__ dinv,
                                                             __nv_bfloat16* __restrict__ yh,
-                                                            __nv_bfloat16* __restrict__ yl,
+                                                            __nv_bfloat16* __restrict__ yl, int ys, int yo,
                                                             double* __restrict__ part) {
   __shared__ f2 Xs[64][65];
   __shared__ float Tr[SPC][65], Ti[SPC][65];
@@ -442,16 +452,16 @@ __global__ void __launch_bounds__(256) block_solve_c_kernel(const float* __restr
     if (m < C) {
       __nv_bfloat16 h, l;
       split_bf16(yr[j], h, l);
-      yh[(long)m * 128 + r] = h;
-      yl[(long)m * 128 + r] = l;
+      yh[(long)m * ys + yo + r] = h;
+      yl[(long)m * ys + yo + r] = l;
       split_bf16(yi[j], h, l);
-      yh[(long)m * 128 + 64 + r] = h;
-      yl[(long)m * 128 + 64 + r] = l;
-      yh[(long)(C + m) * 128 + r] = h;
-      yl[(long)(C + m) * 128 + r] = l;
+      yh[(long)m * ys + yo + 64 + r] = h;
+      yl[(long)m * ys + yo + 64 + r] = l;
+      yh[(long)(C + m) * ys + yo + r] = h;
+      yl[(long)(C + m) * ys + yo + r] = l;
       split_bf16(-yr[j], h, l);
-      yh[(long)(C + m) * 128 + 64 + r] = h;
-      yl[(long)(C + m) * 128 + 64 + r] = l;
+      yh[(long)(C + m) * ys + yo + 64 + r] = h;
+      yl[(long)(C + m) * ys + yo + 64 + r] = l;
     }
   }
   __syncthreads();
@@ -526,8 +536,8 @@ Bufs carve(void* scratch, int n, int C) {
   b.pl = ar.take<__nv_bfloat16>(sq);
   b.oh = ar.take<__nv_bfloat16>(oc);
   b.ol = ar.take<__nv_bfloat16>(oc);
-  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 64);
-  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 64);
+  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 64 * GB);
+  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 64 * GB);
   b.t = ar.take<float>(2 * oc);
   b.linv32 = ar.take<float>((size_t)b.nblk * 64 * 64);
   b.part = ar.take<double>((size_t)b.nblk * C);
@@ -541,14 +551,31 @@ int grid_of(cdwac_ctx* ctx, long work) {
 
 template <bool SUB>
 cdwac_status gemm(cdwac_ctx* ctx, const GemmMaps& maps, int M, int N, int k_tiles, int a_x0, int a_y0, float* out,
-                  long ld, int row_off, cudaStream_t st) {
+                  long ld, int row_off, cudaStream_t st, int b_x0 = 0) {
   if (M <= 0 || N <= 0) return CDWAC_OK;
   CDWAC_CUDA_TRY(ctx, cudaFuncSetAttribute(tc_gemm_kernel<SUB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
   const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-  tc_gemm_kernel<SUB><<<mt * nt, 384, SMEM, st>>>(maps, M, N, k_tiles, a_x0, a_y0, 0, out, ld, row_off,
+  tc_gemm_kernel<SUB><<<mt * nt, 384, SMEM, st>>>(maps, M, N, k_tiles, a_x0, a_y0, b_x0, 0, out, ld, row_off,
                                                   ctx->d_status);
   CDWAC_LAUNCH_CHECK(ctx);
   return CDWAC_OK;
+}
+
+// The updates after block step blk of the blocked substitution, with blocks taken in groups of GB (512 rows): the
+// rows of the rest of blk's group get Y_blk alone (K = 64 columns of the factor, kpb K-tiles of 64 per block),
+// and after the last block of a group every row below the group gets the whole group's Y at once
+// (K = 64 x GB), so the RHS matrix T below the group is read and written once per group instead of once per block.
+cdwac_status group_update(cdwac_ctx* ctx, const GemmMaps& upd, int n, int C, int blk, int nblk, int kpb, float* t,
+                          long ld, cudaStream_t st) {
+  const int g = blk / GB, gend = std::min(nblk, (g + 1) * GB), r1 = (blk + 1) * 64;
+  if (r1 >= n) return CDWAC_OK;
+  const int kw = 64 * kpb;   // factor (and Y) columns per block
+  if (blk + 1 < gend) {
+    const int rend = std::min(n, gend * 64);
+    return gemm<true>(ctx, upd, rend - r1, 2 * C, kpb, blk * kw, r1, t, ld, r1, st, (blk % GB) * kw);
+  }
+  const int nb = blk + 1 - g * GB;
+  return gemm<true>(ctx, upd, n - r1, 2 * C, kpb * nb, g * GB * kw, r1, t, ld, r1, st, 0);
 }
 
 }  // namespace
@@ -570,8 +597,8 @@ CBufs carve_c(void* scratch, int n, int C) {
   const size_t sq = (size_t)n * 2 * b.npad;
   b.lh = ar.take<__nv_bfloat16>(sq);
   b.ll = ar.take<__nv_bfloat16>(sq);
-  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 128);
-  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 128);
+  b.yh = ar.take<__nv_bfloat16>((size_t)2 * C * 128 * GB);
+  b.yl = ar.take<__nv_bfloat16>((size_t)2 * C * 128 * GB);
   b.t = ar.take<float>((size_t)2 * C * b.npad);
   b.linv32 = ar.take<f2>((size_t)b.nblk * 64 * 64);
   b.part = ar.take<double>((size_t)b.nblk * C * 2);
@@ -581,7 +608,7 @@ CBufs carve_c(void* scratch, int n, int C) {
 
 size_t wsolve_tc_c_scratch_bytes(int n, int n_cols) {
   const size_t npad = ((size_t)n + 63) / 64 * 64, nblk = npad / 64;
-  return 2 * ((size_t)n * 2 * npad * 2 + 256) + 2 * ((size_t)2 * n_cols * 128 * 2 + 256) +
+  return 2 * ((size_t)n * 2 * npad * 2 + 256) + 2 * ((size_t)2 * n_cols * 128 * GB * 2 + 256) +
          ((size_t)2 * n_cols * npad * 4 + 256) + (nblk * 64 * 64 * 8 + 256) + (nblk * n_cols * 16 + 256) + 1024;
 }
 
@@ -608,15 +635,14 @@ cdwac_status wsolve_tc_c(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const 
   }
   GemmMaps upd;
   if (!make_map(&upd.ah, b.lh, n, 2L * b.npad) || !make_map(&upd.al, b.ll, n, 2L * b.npad) ||
-      !make_map(&upd.bh, b.yh, 2 * C, 128) || !make_map(&upd.bl, b.yl, 2 * C, 128))
+      !make_map(&upd.bh, b.yh, 2 * C, 128L * GB) || !make_map(&upd.bl, b.yl, 2 * C, 128L * GB))
     return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the complex W solve (n=%d, C=%d)", n, C);
   cdwac_status rc;
   for (int blk = 0; blk < b.nblk; ++blk) {
     block_solve_c_kernel<<<(C + SPC - 1) / SPC, 256, 0, st>>>(b.t, ld, n, C, blk, b.linv32, dinv, b.yh, b.yl,
-                                                               b.part);
+                                                               128 * GB, 128 * (blk % GB), b.part);
     CDWAC_LAUNCH_CHECK(ctx);
-    const int r1 = (blk + 1) * 64;
-    if (r1 < n && (rc = gemm<true>(ctx, upd, n - r1, 2 * C, 2, blk * 128, r1, b.t, ld, r1, st))) return rc;
+    if ((rc = group_update(ctx, upd, n, C, blk, b.nblk, 2, b.t, ld, st))) return rc;
   }
   if (dtype == CDWAC_F64)
     w_reduce_c_kernel<double><<<C, 256, 0, st>>>(b.part, b.nblk, C, n, (const double*)O,
@@ -633,7 +659,7 @@ cdwac_status wsolve_tc_c(cdwac_ctx* ctx, const cplx* L, const cplx* dinv, const 
 size_t wsolve_tc_scratch_bytes(int n, int n_cols) {
   const size_t npad = ((size_t)n + 63) / 64 * 64, nblk = npad / 64;
   const size_t sq = (size_t)n * npad, oc = (size_t)n_cols * npad;
-  return 4 * (sq * 2 + 256) + 2 * (oc * 2 + 256) + 2 * ((size_t)2 * n_cols * 64 * 2 + 256) + (2 * oc * 4 + 256) +
+  return 4 * (sq * 2 + 256) + 2 * (oc * 2 + 256) + 2 * ((size_t)2 * n_cols * 64 * GB * 2 + 256) + (2 * oc * 4 + 256) +
          (nblk * 64 * 64 * 4 + 256) + (nblk * n_cols * 8 + 256) + 1024;
 }
 
@@ -663,16 +689,16 @@ cdwac_status wsolve_tc(cdwac_ctx* ctx, const double* L, const double* dinv, cons
   if (!make_map(&pio.ah, b.ph, n, b.npad) || !make_map(&pio.al, b.pl, n, b.npad) ||
       !make_map(&pio.bh, b.oh, C, b.npad) || !make_map(&pio.bl, b.ol, C, b.npad) ||
       !make_map(&upd.ah, b.lh, n, b.npad) || !make_map(&upd.al, b.ll, n, b.npad) ||
-      !make_map(&upd.bh, b.yh, 2 * C, 64) || !make_map(&upd.bl, b.yl, 2 * C, 64))
+      !make_map(&upd.bh, b.yh, 2 * C, 64L * GB) || !make_map(&upd.bl, b.yl, 2 * C, 64L * GB))
     return set_error(ctx, CDWAC_ERR_CUDA, "cuTensorMapEncodeTiled failed for the W solve (n=%d, C=%d)", n, C);
   cdwac_status rc;
   // second half of T: Pi O
   if ((rc = gemm<false>(ctx, pio, n, C, b.npad / BK, 0, 0, b.t + (long)C * ld, ld, 0, st))) return rc;
   for (int blk = 0; blk < b.nblk; ++blk) {
-    block_solve_kernel<<<(C + SP - 1) / SP, 256, 0, st>>>(b.t, ld, n, C, blk, b.linv32, dinv, b.yh, b.yl, b.part);
+    block_solve_kernel<<<(C + SP - 1) / SP, 256, 0, st>>>(b.t, ld, n, C, blk, b.linv32, dinv, b.yh, b.yl, 64 * GB,
+                                                          64 * (blk % GB), b.part);
     CDWAC_LAUNCH_CHECK(ctx);
-    const int r1 = (blk + 1) * 64;
-    if (r1 < n && (rc = gemm<true>(ctx, upd, n - r1, 2 * C, 1, blk * 64, r1, b.t, ld, r1, st))) return rc;
+    if ((rc = group_update(ctx, upd, n, C, blk, b.nblk, 1, b.t, ld, st))) return rc;
   }
   w_reduce_kernel<<<(C + 127) / 128, 128, 0, st>>>(b.part, b.nblk, C, cols_per_state, W_out, w_state_stride);
   CDWAC_LAUNCH_CHECK(ctx);
