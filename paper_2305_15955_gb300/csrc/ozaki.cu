@@ -26,14 +26,17 @@
 // tile, one per part of A: the re CTA issues Re += Wr Lr and then Re += -(Wi Li) (negated-A instruction
 // descriptor), the im CTA Im += Wr Li and then Im += Wi Lr.
 //
-// One CTA per 128 x 32 tile of the trailing lower triangle (per part, complex), 256 threads, two CTAs per SM
-// (93-97 KB of shared memory and 256 tensor-memory columns each), so that one CTA's epilogue overlaps the other's
-// loads and MMAs: one elected thread issues TMA (3-D maps over the digit planes, 128-byte swizzle; the tile's L
-// digits stay resident, the W digits stream through a ring), one issues the MMAs, all eight warps drain tensor
-// memory (tcgen05.ld 32x32b; two warps per lane quarter), recombine the levels in 64-bit integers, assemble the
-// FP64 update with integer instructions, stage it in shared memory and update A with coalesced row segments.
-// Every mbarrier wait is bounded; on expiry the kernel records CDWAC_ERR_TIMEOUT, waits for the copies it issued
-// and frees its tensor memory.
+// Real A: `oz_strip_kernel`, one CTA per chunk of 128 x 32 tiles of one 128-row strip (640 threads, one CTA per
+// SM): the strip's W digits stay resident, the L digits and two tensor-memory accumulator sets are double-buffered,
+// one MMA per W digit and k-step with the L digits stacked along N, sixteen independent epilogue warps.
+// Complex A: `oz_update_kernel<true>`, one CTA per 128 x 32 tile and part of A (256 threads, two CTAs per SM with
+// 97 KB of shared memory and 256 tensor-memory columns each, so that one CTA's epilogue overlaps the other's loads
+// and MMAs): the tile's L digits stay resident, the W digits stream through a ring, N-stacked MMAs as above.
+// Both: one elected thread issues TMA (3-D maps over the digit planes, 128-byte swizzle), one issues the MMAs, the
+// epilogue warps drain tensor memory (tcgen05.ld 32x32b), recombine the levels exactly in integers, assemble the
+// FP64 update with integer instructions, stage it per warp in shared memory and update A with coalesced row
+// segments.  Every mbarrier wait is bounded; on expiry a kernel records CDWAC_ERR_TIMEOUT, waits for the copies it
+// issued and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <string.h>
@@ -66,7 +69,8 @@ struct OzCfg {
   static constexpr int B_BYTES = NPART * S * B_TILE;   // every digit of every part of L: 28 KB real, 64 KB complex
   static constexpr int NS = 2;                      // stages of the W-digit ring
   static constexpr int WLOADS = NPART * S;          // W digit planes per tile: Wr digits, then (complex) Wi digits
-  // 61 KB (real) or 97 KB (complex) of dynamic shared memory: two CTAs per SM
+  // 97 KB (complex) of dynamic shared memory: two CTAs per SM (the real update runs by strips, oz_strip_kernel;
+  // the real instance gives the digit and plane sizes)
   static constexpr int SMEM = B_BYTES + NS * A_TILE + 1024;
   static constexpr int MIN_CTAS = 2;
   static constexpr int TMEM_COLS = 256;             // S levels x 32 columns (224 real, 256 complex)

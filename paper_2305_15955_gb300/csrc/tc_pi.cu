@@ -6,9 +6,12 @@
 // split into BF16 planes hi + lo (hi = bf16(x), lo = bf16(x - hi)) and the product is formed from three BF16
 // products hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory (the lo*lo term, ~2^-16 relative, is
 // dropped).  On the imaginary axis -w = 4 D / (xi^2 + D^2) > 0; for complex z the real and imaginary parts of -w
-// give two weighted operands and two launches, which write the real and the imaginary parts of A.
+// give two weighted operands, whose contractions write the real and the imaginary parts of A.
 //
-// Kernel: one CTA per 128 x 128 tile of the lower triangle of A (A is symmetric), 384 threads.  Warp 0 lane 0
+// Two kernels: `tc_syrk256_kernel` on 128 x 256 tiles (the default; described at its definition) and
+// `tc_syrk_kernel` on 128 x 128 tiles (the batch autotuner's alternative), described here.
+//
+// tc_syrk_kernel: one CTA per 128 x 128 tile of the lower triangle of A (A is symmetric), 384 threads.  Warp 0 lane 0
 // drives TMA (cp.async.bulk.tensor, 128-byte swizzle) through a ring of shared-memory stages; warp 1 owns the
 // tensor memory and lane 0 issues tcgen05.mma (M = N = 128, K = 16 per instruction, both operands K-major);
 // tcgen05.commit releases a stage when the MMAs reading it finish.  The hi*hi products of every K-tile (one buffer
