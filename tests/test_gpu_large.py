@@ -1,25 +1,19 @@
-"""The W build at a size whose polarizability spans several 12 x 12 groups of 128 x 128 tiles and more than one wave
-of CTAs on the GPU (N_aux = 2200: 18 row tiles, 171 lower-triangle tiles for 152 SMs, a ragged last row tile of 24,
-N_ov = 32 400 with a ragged K tail), against the oracle on a few frequencies.
+"""The W build at a size whose polarizability spans several groups of tiles and more than one wave of CTAs on the
+GPU (N_aux = 2200: 18 row tiles of 128, 171 lower-triangle 128 x 128 tiles or 90 tiles of 128 x 256 for 152 SMs, a
+ragged last row tile of 24, N_ov = 32 400 with a ragged K tail), against the oracle on a few frequencies.
 
 FP64 path: W(i xi) and W(z) to FP64 rounding.  Mixed path: the tolerance of every table row is derived from the
-split-BF16 error of Pi and the conditioning of I - Pi at that frequency.  With hi = bf16(x) and lo = bf16(x - hi)
-an FP32 operand keeps x - hi - lo <= 2^-17 |x|, the dropped lo*lo product is <= 2^-18 |x y|, and the weighted
-operand S = fp32(w) * x adds two FP32 roundings: every term S_Pk B_Qk of Pi carries a relative error below
-2^-16, with signs that vary from term to term (the tensor-core accumulation runs in chunks of 128 columns summed
-with round-to-nearest, so it adds no bias), and the normwise error of Pi is taken as 2^-16 ||Pi||_2.  The W solves'
-split-BF16 products and FP32 block solves act as a backward error of the same size on the factor.  Together
-u = 2^-15 of ||I - Pi||_2, and first-order perturbation of W_nm = o_m^T [(I - Pi)^-1 - I] o_m bounds
-|dW_nm| <= u kappa(I - Pi) ||(I - Pi)^-1||_2 ||o_m||^2 with kappa the 2-norm condition number, which the test
-evaluates from the oracle's matrices (FP64) with a safety factor of 4.  Near-real points
-among the excitations (kappa ~ 1e4 and more) get a correspondingly loose tolerance; the imaginary axis (kappa of
-order ||Pi||) is held to a fraction of W's size.
+split-BF16 error of Pi and the conditioning of I - Pi at that frequency (mixed_bound.py): near-real points among
+the excitations (kappa ~ 1e4 and more) get a correspondingly loose tolerance; the imaginary axis (kappa of order
+||Pi||) is held to a fraction of W's size.
 """
 import numpy as np
 import pytest
 
 from oracle import cdwac_oracle as o
 from paper_2305_15955_gb300 import inputs
+
+from mixed_bound import w_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -29,8 +23,6 @@ if not torch.cuda.is_available():
 
 from paper_2305_15955_gb300 import cdwac  # noqa: E402
 
-U_BF16X3 = 2.0 ** -15
-SAFETY = 4.0
 
 
 @pytest.fixture(scope="module")
@@ -55,15 +47,6 @@ def _oracle_tables(spec, eps, B, On, xi, zr):
     Wim = o.w_imag_table(B, D, On, xi)
     Wre = o.w_complex_table(B, D, On, zr, np.arange(spec.n_occ))
     return D, Wim, Wre
-
-
-def _w_bound(B, D, On, z, m_idx):
-    """Per-state bound on |dW_nm| over m_idx from a BF16x3 Pi and its condition number (module docstring)."""
-    A = np.eye(B.shape[0]) - o.polarizability(B, D, complex(z))
-    sv = np.linalg.svd(A, compute_uv=False)
-    kappa, inv_norm = sv[0] / sv[-1], 1.0 / sv[-1]
-    on2 = np.sum(On[:, :, m_idx] ** 2, axis=1)                      # [n_states, len(m_idx)]
-    return SAFETY * U_BF16X3 * kappa * inv_norm * on2, kappa
 
 
 def test_fp64_path_at_multi_wave_size(ctx, system):
@@ -94,13 +77,13 @@ def test_mixed_path_at_multi_wave_size_within_derived_bound(ctx, system):
     Wg, Wrg = W.cpu().numpy(), pade.W_real.cpu().numpy()
     m_all = np.arange(spec.n_basis)
     for k, x in enumerate(xi_h):
-        bound, kappa = _w_bound(B, D, On, 1j * x, m_all)
+        bound, kappa = w_bound(B, D, On, 1j * x, m_all)
         err = np.abs(Wg[:, k, :] - Wim[:, k, :])
         assert np.all(err <= bound), (k, kappa, float((err / bound).max()))
         # the bound is not vacuous: on the imaginary axis it holds W to a fraction of its size
         assert np.all(bound.max(axis=1) < 0.05 * np.abs(Wim[:, k, :]).max(axis=1)), (k, kappa)
     m_occ = np.arange(spec.n_occ)
     for j, z in enumerate(zr):
-        bound, kappa = _w_bound(B, D, On, z, m_occ)
+        bound, kappa = w_bound(B, D, On, z, m_occ)
         err = np.abs(Wrg[:, j, :] - Wre[:, j, :])
         assert np.all(err <= bound), (j, z, kappa, float((err / bound).max()))
