@@ -741,7 +741,7 @@ static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, c
     return CDWAC_OK;
   };
   cdwac_status rc;
-  double e = en, e_new = e, s;
+  double e = en, e_new = e, s = 0.0;
   for (int it = 1; it <= max_iter; ++it) {
     if ((rc = resig(e, &s))) return rc;
     e_new = en + sh + s;
@@ -757,7 +757,7 @@ static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, c
   bool found = false;
   double be = 0, bz = 0;
   auto f = [&](double w, double* v) -> cdwac_status {
-    double sv;
+    double sv = 0.0;
     cdwac_status r = resig(w, &sv);
     *v = w - en - sh - sv;
     return r;
