@@ -733,7 +733,7 @@ static cdwac_status qp_plain_cd_state(cdwac_ctx* ctx, const cdwac_system* sub, c
   };
   const double hstep = 1e-5;
   auto zfac = [&](double e, double* z) -> cdwac_status {
-    double a, b;
+    double a = 0.0, b = 0.0;
     cdwac_status r;
     if ((r = resig(e + hstep, &a))) return r;
     if ((r = resig(e - hstep, &b))) return r;
