@@ -309,8 +309,8 @@ typedef struct {
  * fastest, the tile configuration of the tensor-core kernels: the Pi output tile width (128 x 256 or 128 x 128),
  * its tile-group size (output tiles ordered in groups of G row blocks; G in {4, 8, 12, 16}) and the number of CTA
  * waves (1, 2 or 3) the real trailing update's 128-row strips are cut into; it keeps the fastest.  The group size
- * and the waves change no result bit; the two Pi tile widths sum the same products in a different order at the
- * 2048-column chunk boundaries (FP32 rounding).  Choices are appended to the file named by the environment
+ * and the waves change no result bit; the two Pi tile widths sum the same products in differently chunked FP32
+ * accumulations (FP32 rounding).  Choices are appended to the file named by the environment
  * variable CDWAC_TUNE_CACHE (if set) and read back by later processes.  `chosen` (may be NULL; five ints)
  * receives {lanes, lookahead, Pi tile-group size, Pi tile width, update waves}.  The precision and parameters
  * are the same for every item. */
